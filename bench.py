@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark: CI tests/sec and PC-stable skeleton time on one GB300.
+
+One step = one whole skeleton (every depth: snapshot, edge list, CI tests,
+removal) of the workload, through the C ABI, with the data already resident in
+HBM.  Throughput counts the tests the sequential Algorithm 1 runs (redundant
+tests of the parallel pool are not counted).  The L2 is flushed (a 256 MB
+device write) before every timed step, outside its events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mid|small|large|depth0|batched]
+                    [--form pool|plain] [--gs G] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica of the workload on its
+own GPU (weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CI tests/sec & PC-stable skeleton time, 1 GB300, batched/INT8 vs plain GPU form"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="mid")
+    ap.add_argument("--form", choices=["pool", "plain"], default="pool")
+    ap.add_argument("--gs", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def load_workload(name):
+    import bnsynth
+    if name == "batched":
+        probs = bnsynth.batched_workload(256)
+        return {"kind": "batch", "probs": [(d, a) for d, a, _ in probs], "alpha": 0.05, "max_depth": -1}
+    data, ar, alpha, md, _ = bnsynth.workload(name)
+    return {"kind": "single", "data": data, "ar": ar, "alpha": alpha, "max_depth": md}
+
+
+def workload_config(name, w, args):
+    cfg = {"workload": name, "form": args.form, "group_size": args.gs or 4,
+           "l2": "flushed by a 256 MB device write before each timed step"}
+    if w["kind"] == "single":
+        n, N = w["data"].shape
+        cfg.update(n_vars=n, n_samples=N, alpha=w["alpha"], max_depth=w["max_depth"],
+                   arities=sorted({int(a) for a in w["ar"]}))
+    else:
+        cfg.update(problems=len(w["probs"]), n_vars_total=sum(d.shape[0] for d, _ in w["probs"]),
+                   samples_total=sum(d.shape[1] for d, _ in w["probs"]), alpha=w["alpha"],
+                   max_depth=w["max_depth"])
+    return cfg
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile(prefix="clocks", suffix=".csv", delete=False)
+        self.idx = gpu_index
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+def oracle_rate(w, stats, budget_s=10.0, max_depths=None):
+    """Time the CPU oracle on a bounded sample of the workload; returns dict."""
+    import numpy as np
+    import oracle
+    if w["kind"] == "single" and w["data"].shape[0] <= 64:
+        # the whole skeleton, repeated until the budget is used
+        t0 = time.perf_counter()
+        tests, runs = 0, 0
+        while True:
+            r = oracle.pc_stable(w["data"], w["ar"], w["alpha"], w["max_depth"])
+            tests += r.n_tests
+            runs += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        dt = time.perf_counter() - t0
+        return {"value": tests / dt, "unit": "tests/s", "cores": 1, "kind": "oracle",
+                "sample": f"{runs} full sequential skeletons of the workload ({tests // runs} tests each)"}
+    # per-depth sample: random tests of the right size, weighted by the GPU's oracle-equivalent counts
+    if w["kind"] == "single":
+        sets = [(w["data"], w["ar"])]
+    else:
+        sets = w["probs"][:16]
+    rng = np.random.default_rng(0)
+    per_depth = stats["tests_oracle"]
+    total = sum(per_depth)
+    sec_per_test = []
+    done = 0
+    for d, cnt in enumerate(per_depth):
+        if cnt == 0:
+            sec_per_test.append(0.0)
+            continue
+        share = budget_s * cnt / total
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            data, ar = sets[k % len(sets)]
+            v = rng.permutation(data.shape[0])[: d + 2]
+            oracle.ci_test(data, ar, int(v[0]), int(v[1]), [int(t) for t in v[2:]])
+            k += 1
+            if time.perf_counter() - t0 >= share or k >= 200000:
+                break
+        sec_per_test.append((time.perf_counter() - t0) / k)
+        done += k
+    est = sum(c * s for c, s in zip(per_depth, sec_per_test))
+    return {"value": total / est, "unit": "tests/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} single CI tests drawn per depth in proportion to the skeleton's "
+                      f"test mix (depths 0..{len(per_depth) - 1}), sequential"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, w, name, rank, world):
+    if rank != 0:
+        return
+    import oracle  # the CPU oracle is this tier's reference program
+    oracle.build()
+    import numpy as np
+    # a bounded sample per step: the whole small skeletons, else 2 s of sampled tests
+    def one_step():
+        if w["kind"] == "single" and w["data"].shape[0] <= 64:
+            t0 = time.perf_counter()
+            r = oracle.pc_stable(w["data"], w["ar"], w["alpha"], w["max_depth"])
+            return r.n_tests, time.perf_counter() - t0, "one full sequential skeleton per step"
+        sets = [(w["data"], w["ar"])] if w["kind"] == "single" else w["probs"][:16]
+        rng = np.random.default_rng(1)
+        t0 = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t0 < 2.0:
+            data, ar = sets[k % len(sets)]
+            d = int(rng.integers(0, 3))
+            v = rng.permutation(data.shape[0])[: d + 2]
+            oracle.ci_test(data, ar, int(v[0]), int(v[1]), [int(t) for t in v[2:]])
+            k += 1
+        return k, time.perf_counter() - t0, "2 s of sampled single CI tests (depths 0-2) per step"
+    for _ in range(args.warmup):
+        one_step()
+    tests, secs, what = 0, 0.0, ""
+    for _ in range(args.steps):
+        t, s, what = one_step()
+        tests += t
+        secs += s
+    val = tests / secs
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "tests/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(name, w, args),
+            "cpu_baseline": {"value": val, "unit": "tests/s", "cores": 1, "kind": "oracle", "sample": what},
+            "e2e": {"value": val, "unit": "tests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    name = args.workload
+    w = load_workload(name)
+    if args.impl == "reference":
+        return run_reference(args, w, name, rank, world)
+
+    import numpy as np
+    import torch
+    import paper_2212_04259_gb300 as F
+    from paper_2212_04259_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    stream = torch.cuda.current_stream()
+    gs = args.gs
+    if w["kind"] == "single":
+        data_dev = torch.from_numpy(w["data"]).cuda()
+        handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local)]
+        F.fbn_set_stream(handles[0], stream)
+        outs = [torch.zeros((w["data"].shape[0],) * 2, dtype=torch.uint8, device="cuda")]
+    else:
+        handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local)
+                   for d, a in w["probs"]]
+        F.fbn_set_stream(handles[0], stream)
+        outs = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8, device="cuda") for d, _ in w["probs"]]
+
+    def step():
+        if w["kind"] == "single":
+            F.fbn_learn_skeleton(handles[0], w["alpha"], w["max_depth"], adj_out=outs[0])
+        else:
+            F.fbn_learn_skeleton_batch(handles, w["alpha"], w["max_depth"], adj_out=outs)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    evs = []
+    stats_acc = None
+    torch.cuda.synchronize()
+    barrier()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+        st = F.fbn_get_stats(handles[0])
+        if stats_acc is None:
+            stats_acc = {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
+            stats_acc["test_ms"] = list(st["test_ms"])
+        else:
+            stats_acc["test_ms"] = [a + b for a, b in zip(stats_acc["test_ms"], st["test_ms"])]
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    st = F.fbn_get_stats(handles[0])
+    tests = sum(st["tests_oracle"])
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * tests / (ms / 1e3)
+
+    # roofline of the CI-test kernel: algorithmic sample bytes (d+2) N per oracle-equivalent test
+    if w["kind"] == "single":
+        Ns = [w["data"].shape[1]]
+    else:
+        Ns = [d.shape[1] for d, _ in w["probs"]]
+    meanN = sum(Ns) / len(Ns)
+    alg_bytes = sum(c * (d + 2) * meanN for d, c in enumerate(st["tests_oracle"]))
+    test_ms = sum(stats_acc["test_ms"]) / args.steps
+    achieved = alg_bytes / (test_ms / 1e3) / 1e9 if test_ms > 0 else 0.0
+    try:
+        peaks = json.load(open(PEAKS))
+        peak, peak_src = float(peaks["hbm_gbs"]), "of measured"
+    except Exception:
+        peak, peak_src = FALLBACK_HBM_GBS, "of fallback"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "peak_source": peak_src, "kernel": "k_pool" if args.form == "pool" else "k_plain",
+                "kernel_ms_per_step": test_ms, "algorithmic_bytes_per_step": alg_bytes}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if True:  # every rank measures its own replica
+        if w["kind"] == "single":
+            host = torch.from_numpy(w["data"]).pin_memory()
+            n = w["data"].shape[0]
+            adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
+            e2e_ms = []
+            d2h = 0
+            for _ in range(args.e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                h2 = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local)
+                F.fbn_learn_skeleton(h2, w["alpha"], w["max_depth"], adj_out=adj_host)
+                seps = F.fbn_export_sepsets(h2)
+                F.fbn_destroy(h2)
+                torch.cuda.synchronize()
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+                d2h = n * n + n * n * 12 + 4 * sum(len(s) for s in seps.values())
+            e2e_v = tests / (statistics.median(e2e_ms) / 1e3)
+            e2e = {"value": world * e2e_v, "unit": "tests/s", "h2d_bytes_per_step": int(host.numel() + n),
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.median(e2e_ms)}
+        else:
+            hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
+            e2e_ms = []
+            for _ in range(args.e2e_steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                hs = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local)
+                      for hh, (_, a) in zip(hosts, w["probs"])]
+                F.fbn_learn_skeleton_batch(hs, w["alpha"], w["max_depth"])
+                for hh in hs:
+                    F.fbn_destroy(hh)
+                torch.cuda.synchronize()
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            nn = sum(d.shape[0] ** 2 for d, _ in w["probs"])
+            e2e = {"value": world * tests / (statistics.median(e2e_ms) / 1e3), "unit": "tests/s",
+                   "h2d_bytes_per_step": int(sum(h.numel() for h in hosts)), "d2h_bytes_per_step": int(13 * nn),
+                   "ms_per_step": statistics.median(e2e_ms)}
+
+    # the plain edge-level GPU form on the same workload, for comparison
+    plain = None
+    if not args.no_plain and args.form == "pool":
+        if w["kind"] == "single":
+            hp = F.fbn_create(data_dev, w["ar"], form="plain", device=local)
+            F.fbn_set_stream(hp, stream)
+            F.fbn_learn_skeleton(hp, w["alpha"], w["max_depth"], adj_out=outs[0])
+            pm = []
+            for _ in range(max(2, min(args.steps, 5))):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                F.fbn_learn_skeleton(hp, w["alpha"], w["max_depth"], adj_out=outs[0])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                pm.append(e0.elapsed_time(e1))
+            sp = F.fbn_get_stats(hp)
+            pms = sum(pm) / len(pm)
+            plain = {"value": world * sum(sp["tests_oracle"]) / (pms / 1e3), "ms_per_step": pms,
+                     "tests_executed": sum(sp["tests"])}
+            F.fbn_destroy(hp)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        cpu = oracle_rate(w, st)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+                "config": workload_config(name, w, args), "clocks": clk, "e2e": e2e,
+                "gpu_launches": int(st["launches"]) * args.steps, "roofline": roofline,
+                "cpu_baseline": cpu, "plain_form": plain,
+                "tests_per_step": {"oracle_equivalent": tests, "executed": sum(st["tests"]),
+                                   "per_depth_oracle": st["tests_oracle"]},
+                "skeleton_ms": ms, "wall_s": wall}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * fbn.h -- C ABI of the GB300 PC-stable skeleton engine (Fast-BNS method,
+ * arXiv 2212.04259) for discrete data with the G^2 conditional-independence
+ * test.
+ *
+ * Every entry point returns an int status: FBN_OK (0) on success, a negative
+ * FBN_E* code otherwise; fbn_last_error() then gives a one-line reason.  A
+ * handle is not thread-safe: calls on one handle must not overlap.  Outputs go
+ * to caller-provided buffers.  Pointers documented as "host or device" are
+ * classified with cudaPointerGetAttributes; device pointers must belong to the
+ * handle's device.  No function falls back to the CPU: without a usable CUDA
+ * device, fbn_create returns FBN_ECUDA.
+ *
+ * Notation: n variables V_0..V_{n-1}, N samples, r_v = arity of V_v.  A CI test
+ * I(X, Y | S) builds the contingency table N_xyz over all samples and reduces
+ * it to G^2, df and a chi-square p-value (Section III-B).
+ */
+#ifndef FBN_H
+#define FBN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FBN_OK        0
+#define FBN_EINVAL   (-1)  /* bad argument (null pointer, size or index out of range) */
+#define FBN_EDATA    (-2)  /* a data value is >= its variable's arity */
+#define FBN_ENOMEM   (-3)  /* device or host allocation failed */
+#define FBN_ECUDA    (-4)  /* a CUDA runtime call or kernel failed */
+#define FBN_ETOOBIG  (-5)  /* a contingency table exceeds the supported cell count */
+#define FBN_ETIMEOUT (-6)  /* a bounded device wait gave up */
+#define FBN_ENUMERIC (-7)  /* the p-value iteration did not converge */
+
+/* ---- options ----------------------------------------------------------- */
+#define FBN_FORM_POOL  0   /* CI-level work pool: persistent kernel, atomic chunk claims (Section IV-B) */
+#define FBN_FORM_PLAIN 1   /* edge-level form: one CTA per edge, one launch per depth (Section IV-A) */
+
+#define FBN_DEPTH0_AUTO 0  /* tensor-core one-hot Gram when the problem is large enough, else histogram */
+#define FBN_DEPTH0_HIST 1  /* depth 0 through the shared-memory histogram path */
+#define FBN_DEPTH0_GRAM 2  /* depth 0 through the tcgen05 one-hot Gram */
+
+typedef struct fbn_options {
+    int32_t form;        /* FBN_FORM_POOL (default) or FBN_FORM_PLAIN */
+    int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default */
+    int32_t depth0;      /* FBN_DEPTH0_* */
+    int32_t device;      /* CUDA device ordinal; -1 = the current device */
+    int32_t reserved[12];/* must be zero */
+} fbn_options;
+
+/* Per-depth counters of the last fbn_learn_skeleton call. */
+#define FBN_MAX_DEPTHS 64
+typedef struct fbn_stats {
+    int32_t depths;                         /* depths that ran */
+    int32_t reserved;
+    int64_t launches;                       /* kernels launched by the call */
+    int64_t edges[FBN_MAX_DEPTHS];          /* edges with at least one test at depth d */
+    int64_t tests[FBN_MAX_DEPTHS];          /* CI tests executed, redundant ones included */
+    int64_t tests_oracle[FBN_MAX_DEPTHS];   /* tests the sequential Algorithm 1 runs (gs = 1) */
+    int64_t removed[FBN_MAX_DEPTHS];        /* edges removed at depth d */
+    double  ms[FBN_MAX_DEPTHS];             /* device time of depth d (CUDA events) */
+    double  test_ms[FBN_MAX_DEPTHS];        /* device time of depth d's CI-test kernel */
+} fbn_stats;
+
+typedef struct fbn_handle fbn_handle;
+
+/* fbn_create -- load a discrete data set (Section IV-C, cache-friendly storage:
+ * one row per variable).
+ *   data     : uint8 [n_vars][n_samples], variable-major, host or device memory;
+ *              copied into the handle's padded device store (row stride a
+ *              multiple of 256 bytes), the caller keeps ownership.
+ *   arities  : uint8 [n_vars], host memory, 2 <= r_v <= 255.
+ *   opt      : nullable; zero-initialised fields take defaults.
+ *   out      : receives the handle.
+ * Errors: FBN_EINVAL (null pointer, n_vars < 2, n_samples < 1 or >= 2^31,
+ * arity outside [2, 255], nonzero reserved option), FBN_EDATA (a value >= its
+ * arity; the handle is not created), FBN_ENOMEM, FBN_ECUDA.  When the call
+ * fails before a handle exists, fbn_last_error(NULL) gives the reason. */
+int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples,
+               const uint8_t* arities, const fbn_options* opt, fbn_handle** out);
+
+/* fbn_set_stream -- run the handle's work on a caller-owned cudaStream_t
+ * (passed as void*; NULL selects the handle's own stream).  The stream must
+ * outlive its use by the handle. */
+int fbn_set_stream(fbn_handle* h, void* stream);
+
+/* fbn_ci_test -- one conditional-independence test I(X, Y | Z) (Section III-B):
+ * contingency table over all samples, marginals, G^2 = 2 sum N ln(N/E),
+ * df = (r_x - 1)(r_y - 1) prod_{k in Z} r_k, p = P(chi^2_df > G^2).
+ *   x, y : variable indices, x != y;  z : nz distinct indices (host), none
+ *   equal to x or y, nz >= 0 (z may be NULL when nz == 0).
+ *   g2, df, p : host outputs (double).
+ * Errors: FBN_EINVAL, FBN_ETOOBIG (table over the cell limit), FBN_ENUMERIC,
+ * FBN_ECUDA.  Synchronises the handle's stream. */
+int fbn_ci_test(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz,
+                double* g2, double* df, double* p);
+
+/* fbn_ci_table -- the exact contingency table of I(X, Y | Z) (Section III-B),
+ * int32 counts in host memory, layout counts[(zi * r_x + xv) * r_y + yv] where
+ * zi is the mixed-radix index of the Z values in the order given, z[0] most
+ * significant.  cap is the capacity of counts in elements; the call returns
+ * FBN_EINVAL if cap is smaller than the cell count r_x r_y prod r_z. */
+int fbn_ci_table(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz,
+                 int32_t* counts, int64_t cap);
+
+/* fbn_learn_skeleton -- the first step of PC-stable (Algorithm 1): start from
+ * the complete graph; at each depth d = 0, 1, ... snapshot the adjacency sets
+ * a(V), test every remaining edge i<j against conditioning sets of size d
+ * drawn from a(V_i)\{V_j} and then a(V_j)\{V_i} (the two endpoints grouped,
+ * Section IV-C), remove the edge at the end of the depth if some test accepts
+ * independence (p > alpha) and keep the first accepting set (lowest rank in
+ * that order) as its separating set; stop when no edge has a side with at
+ * least d candidates or when d > max_depth (max_depth = -1: unbounded).
+ *   adj_out : uint8 [n][n], host or device, receives the symmetric 0/1
+ *             adjacency of the skeleton (zero diagonal).  Nullable.
+ * Separating sets stay in the handle until the next call or fbn_destroy; read
+ * them with fbn_get_sepset / fbn_export_sepsets.
+ * Errors: FBN_EINVAL (alpha outside (0, 1), max_depth < -1), FBN_ETOOBIG,
+ * FBN_ENOMEM, FBN_ENUMERIC, FBN_ECUDA. */
+int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* adj_out);
+
+/* fbn_learn_skeleton_batch -- fbn_learn_skeleton on k independent handles that
+ * share one device and one stream (the first handle's): each depth runs one
+ * work pool over the edges of every problem still active.  Results are the
+ * same as k separate calls.  adj_out: array of k nullable pointers, each as in
+ * fbn_learn_skeleton.  Errors as fbn_learn_skeleton; the handles' devices must
+ * match. */
+int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth,
+                             uint8_t* const* adj_out);
+
+/* fbn_get_sepset -- separating set of the pair (i, j) from the last skeleton
+ * (Algorithm 1, SepSet): returns |S| (0 for an empty set) and writes up to cap
+ * members, ascending, into buf (host); returns -1 if i and j are still
+ * adjacent, FBN_EINVAL for bad indices or before any skeleton was learnt. */
+int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, int32_t cap);
+
+/* fbn_export_sepsets -- every separating set at once, in CSR form (host):
+ *   pairs   : int32 [n_removed][2] (i < j), ascending by (i, j);
+ *   offsets : int64 [n_removed + 1];  members : int32 [offsets[n_removed]].
+ * Call with NULL buffers to get the sizes in *n_removed and *n_members. */
+int fbn_export_sepsets(const fbn_handle* h, int64_t* n_removed, int64_t* n_members,
+                       int32_t* pairs, int64_t* offsets, int32_t* members);
+
+/* fbn_get_stats -- per-depth counters of the last skeleton call. */
+int fbn_get_stats(const fbn_handle* h, fbn_stats* out);
+
+/* fbn_last_error -- reason for the last failure on h (or of the last failed
+ * fbn_create when h is NULL).  The string lives until the next call on h. */
+const char* fbn_last_error(const fbn_handle* h);
+
+/* fbn_destroy -- free the handle and its device memory (NULL is a no-op). */
+void fbn_destroy(fbn_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBN_H */

@@ -1,0 +1,758 @@
+// fbn_api.cu -- host engine and C ABI (include/fbn.h) of the GB300 PC-stable
+// skeleton library.  The depth loop of Algorithm 1 runs here; every step of a
+// depth (snapshot, edge list, CI tests, removal) is a kernel in fbn_kernels.cu.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fbn.h"
+#include "fbn_launch.h"
+
+using namespace fbn;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr size_t kSmemBytes = 108 * 1024;   // dynamic shared memory of a test CTA (2 CTAs / SM)
+constexpr int kDefaultGs = 4;
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void dfree(void* p)
+{
+    if (p) cudaFree(p);
+}
+
+// ---- small kernels of the host engine ------------------------------------
+__global__ void k_validate(const uint8_t* data, int64_t ld, int n, int64_t N, const uint8_t* ar,
+                           unsigned long long* first_bad)
+{
+    const int v = blockIdx.y;
+    const uint8_t r = ar[v];
+    const uint8_t* row = data + (long long)v * ld;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        if (row[s] >= r) atomicMin(first_bad, (unsigned long long)v * (unsigned long long)N + s);
+    }
+}
+
+__global__ void k_init_graph(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
+                             int total_vertices)
+{
+    const int g = blockIdx.x;
+    if (g >= total_vertices) return;
+    const int p = vtx_prob[g];
+    const ProblemDev P = probs[p];
+    const int i = g - vtx_first[p];
+    for (int j = threadIdx.x; j < P.n; j += blockDim.x) {
+        P.adj[(long long)i * P.n + j] = (uint8_t)(i != j);
+        P.sep_len[(long long)i * P.n + j] = -1;
+        P.sep_off[(long long)i * P.n + j] = 0;
+    }
+}
+
+}  // namespace
+
+// ---- workspace shared by the depth loop ----------------------------------
+struct Workspace {
+    long long edge_cap = 0;
+    EdgeWork* edges = nullptr;
+    unsigned long long* min_accept = nullptr;
+    int32_t* sorted = nullptr;
+    long long ord_cap = 0;
+    unsigned long long *hist = nullptr, *alive = nullptr, *base = nullptr, *cursor = nullptr;
+    DepthCounters* d_ctr = nullptr;
+    DepthCounters* h_ctr = nullptr;   // pinned
+    long long* binom = nullptr;
+    int brows = 0;
+    int vtx_cap = 0, prob_cap = 0;
+    int32_t *vtx_prob = nullptr, *vtx_first = nullptr;
+    ProblemDev* probs = nullptr;
+    int32_t* sep_pool = nullptr;
+    long long sep_cap = 0;
+    int* gscratch = nullptr;
+    long long gscratch_total = 0;
+    cudaEvent_t ev[FBN_MAX_DEPTHS + 1] = {};
+    cudaEvent_t kev[2] = {};
+    bool events = false;
+
+    void release()
+    {
+        dfree(edges); dfree(min_accept); dfree(sorted);
+        dfree(hist); dfree(alive); dfree(base); dfree(cursor);
+        dfree(d_ctr);
+        if (h_ctr) cudaFreeHost(h_ctr);
+        dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
+        dfree(sep_pool); dfree(gscratch);
+        if (events) {
+            for (auto& e : ev) cudaEventDestroy(e);
+            for (auto& e : kev) cudaEventDestroy(e);
+        }
+        *this = Workspace();
+    }
+};
+
+struct fbn_handle {
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    fbn_options opt{};
+    int n = 0;
+    int64_t N = 0, ld = 0;
+    int max_arity = 0;
+    std::vector<uint8_t> h_ar;
+    uint8_t* d_data = nullptr;
+    uint8_t* d_ar = nullptr;
+    uint8_t* d_adj = nullptr;
+    int32_t* d_nbr = nullptr;
+    int32_t* d_deg = nullptr;
+    int32_t* d_sep_len = nullptr;
+    int64_t* d_sep_off = nullptr;
+    ProblemDev* d_prob = nullptr;
+    // single-test scratch
+    CiTestDesc* d_ci = nullptr;
+    double* d_ci_out = nullptr;
+    unsigned* d_status = nullptr;
+    int32_t* d_table = nullptr;
+    long long table_cap = 0;
+    int* d_gscratch = nullptr;
+    long long gscratch_ints = 0;
+    CiTestDesc* h_ci = nullptr;   // pinned
+    double* h_ci_out = nullptr;   // pinned
+    unsigned* h_status = nullptr; // pinned
+    // results of the last skeleton
+    bool learnt = false;
+    std::vector<int32_t> sep_len;      // n*n, i<j entries
+    std::vector<int64_t> sep_off;      // n*n offsets into sep_members
+    std::vector<int32_t> sep_members;
+    fbn_stats stats{};
+    Workspace ws;
+    std::string err;
+};
+
+namespace {
+
+int fail(fbn_handle* h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? FBN_ENOMEM : FBN_ECUDA,   \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, int nprob, int total_vtx)
+{
+    if (!ws.d_ctr) {
+        CK(dalloc(&ws.d_ctr, 1));
+        CK(cudaMallocHost((void**)&ws.h_ctr, sizeof(DepthCounters)));
+        for (auto& e : ws.ev) CK(cudaEventCreate(&e));
+        for (auto& e : ws.kev) CK(cudaEventCreate(&e));
+        ws.events = true;
+    }
+    if (edge_cap > ws.edge_cap) {
+        dfree(ws.edges); dfree(ws.min_accept); dfree(ws.sorted);
+        ws.edges = nullptr; ws.min_accept = nullptr; ws.sorted = nullptr; ws.edge_cap = 0;
+        CK(dalloc(&ws.edges, edge_cap));
+        CK(dalloc(&ws.min_accept, edge_cap));
+        CK(dalloc(&ws.sorted, edge_cap));
+        ws.edge_cap = edge_cap;
+    }
+    if (max_n + 1 > ws.brows) {
+        dfree(ws.binom);
+        ws.binom = nullptr;
+        const int rows = max_n + 1;
+        std::vector<long long> B((size_t)rows * kBinomCols, 0);
+        for (int nn = 0; nn < rows; ++nn) {
+            B[(size_t)nn * kBinomCols] = 1;
+            for (int k = 1; k < kBinomCols; ++k) {
+                if (nn == 0) break;
+                const long long a = B[(size_t)(nn - 1) * kBinomCols + k - 1];
+                const long long b = B[(size_t)(nn - 1) * kBinomCols + k];
+                long long s = a + b;
+                if (s > kBinomSat || s < 0) s = kBinomSat;
+                B[(size_t)nn * kBinomCols + k] = s;
+            }
+        }
+        CK(dalloc(&ws.binom, B.size()));
+        CK(cudaMemcpy(ws.binom, B.data(), B.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        ws.brows = rows;
+    }
+    if (total_vtx > ws.vtx_cap) {
+        dfree(ws.vtx_prob); dfree(ws.vtx_first);
+        ws.vtx_prob = nullptr; ws.vtx_first = nullptr; ws.vtx_cap = 0;
+        CK(dalloc(&ws.vtx_prob, total_vtx));
+        CK(dalloc(&ws.vtx_first, std::max(nprob, total_vtx)));
+        ws.vtx_cap = total_vtx;
+    }
+    if (nprob > ws.prob_cap) {
+        dfree(ws.probs);
+        ws.probs = nullptr; ws.prob_cap = 0;
+        CK(dalloc(&ws.probs, nprob));
+        ws.prob_cap = nprob;
+    }
+    return FBN_OK;
+}
+
+int ensure_order(fbn_handle* h, Workspace& ws, long long maxc)
+{
+    if (maxc + 1 <= ws.ord_cap) return FBN_OK;
+    dfree(ws.hist); dfree(ws.alive); dfree(ws.base); dfree(ws.cursor);
+    ws.hist = ws.alive = ws.base = ws.cursor = nullptr;
+    ws.ord_cap = 0;
+    const long long cap = std::max(maxc + 1, 1024LL);
+    CK(dalloc(&ws.hist, cap));
+    CK(dalloc(&ws.alive, cap));
+    CK(dalloc(&ws.base, cap));
+    CK(dalloc(&ws.cursor, cap));
+    ws.ord_cap = cap;
+    return FBN_OK;
+}
+
+int ensure_sep_pool(fbn_handle* h, Workspace& ws, long long need, long long used, cudaStream_t st)
+{
+    if (need <= ws.sep_cap) return FBN_OK;
+    const long long cap = std::max(need, 2 * ws.sep_cap);
+    int32_t* p = nullptr;
+    CK(dalloc(&p, cap));
+    if (ws.sep_pool && used > 0)
+        CK(cudaMemcpyAsync(p, ws.sep_pool, used * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    dfree(ws.sep_pool);
+    ws.sep_pool = p;
+    ws.sep_cap = cap;
+    return FBN_OK;
+}
+
+int ensure_gscratch(fbn_handle* h, Workspace& ws, long long total_ints)
+{
+    if (total_ints <= ws.gscratch_total) return FBN_OK;
+    dfree(ws.gscratch);
+    ws.gscratch = nullptr;
+    ws.gscratch_total = 0;
+    CK(dalloc(&ws.gscratch, total_ints));
+    ws.gscratch_total = total_ints;
+    return FBN_OK;
+}
+
+// Shared-memory ints a test CTA can use for counts of a table of C cells
+// without falling back to a global table.
+bool fits_smem(long long C)
+{
+    const long long budget = (long long)(kSmemBytes / 4);
+    return C + (C * 5) / 4 + 8 <= budget;   // table + marginals bound (r_x, r_y >= 2)
+}
+
+int check_status(fbn_handle* h, unsigned status)
+{
+    if (status & kStatusTooBig) return fail(h, FBN_ETOOBIG, "a contingency table exceeds %lld cells", kMaxCells);
+    if (status & kStatusNumeric) return fail(h, FBN_ENUMERIC, "p-value iteration did not converge");
+    if (status & kStatusSepPool) return fail(h, FBN_ECUDA, "separating-set pool overflow");
+    return FBN_OK;
+}
+
+// The depth loop of Algorithm 1 over one or more problems sharing a stream.
+int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+{
+    fbn_handle* h = hs[0];
+    Workspace& ws = h->ws;
+    cudaStream_t st = h->stream;
+    CK(cudaSetDevice(h->device));
+    long long edge_cap = 0;
+    int max_n = 0, total_vtx = 0;
+    std::vector<ProblemDev> P(k);
+    std::vector<int32_t> vtx_prob, vtx_first(k);
+    for (int p = 0; p < k; ++p) {
+        const fbn_handle* q = hs[p];
+        edge_cap += (long long)q->n * (q->n - 1) / 2;
+        max_n = std::max(max_n, q->n);
+        vtx_first[p] = total_vtx;
+        total_vtx += q->n;
+        for (int v = 0; v < q->n; ++v) vtx_prob.push_back(p);
+        ProblemDev& d = P[p];
+        d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.deg = q->d_deg;
+        d.sep_len = q->d_sep_len; d.sep_off = q->d_sep_off; d.ld = q->ld; d.n = q->n; d.N = (int32_t)q->N;
+        d.max_arity = q->max_arity; d.pad = 0;
+    }
+    int rc = grow_workspace(h, ws, edge_cap, max_n, k, total_vtx);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(ws.probs, P.data(), k * sizeof(ProblemDev), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.vtx_prob, vtx_prob.data(), total_vtx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.vtx_first, vtx_first.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    k_init_graph<<<total_vtx, 256, 0, st>>>(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx);
+    CK(cudaGetLastError());
+    long long launches = 1;
+
+    int dev_sms = 0;
+    CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
+    CK(set_kernel_smem(kSmemBytes));
+    const int bps = std::max(1, pool_blocks_per_sm(kSmemBytes));
+    const int pool_grid = dev_sms * bps;
+    const int gs = h->opt.group_size > 0 ? h->opt.group_size : kDefaultGs;
+    const bool plain = h->opt.form == FBN_FORM_PLAIN;
+
+    fbn_stats stats{};
+    unsigned long long sep_used = 0;
+    for (int d = 0;; ++d) {
+        if (max_depth >= 0 && d > max_depth) break;
+        if (d > kMaxD) return fail(h, FBN_ETOOBIG, "depth %d exceeds the supported %d", d, kMaxD);
+        if (d >= FBN_MAX_DEPTHS) return fail(h, FBN_ETOOBIG, "depth %d exceeds FBN_MAX_DEPTHS", d);
+        DepthCounters c0{};
+        c0.sep_used = sep_used;
+        *ws.h_ctr = c0;
+        CK(cudaEventRecord(ws.ev[d], st));
+        CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
+        launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st);
+        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, d, plain ? 1 : gs, ws.binom, ws.brows,
+                     ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, st);
+        CK(cudaGetLastError());
+        launches += 2;
+        CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        const long long E = (long long)ws.h_ctr->n_edges;
+        if (E == 0) break;   // no edge has a side with >= d candidates (Algorithm 1, last line)
+        const long long maxc = (long long)ws.h_ctr->maxc;
+        const long long max_cells = (long long)ws.h_ctr->max_cells;
+        if (max_cells > kMaxCells)
+            return fail(h, FBN_ETOOBIG, "depth %d may need tables of more than %lld cells", d, kMaxCells);
+        rc = ensure_sep_pool(h, ws, (long long)sep_used + E * d + 1, (long long)sep_used, st);
+        if (rc) return rc;
+
+        PoolArgs a{};
+        a.probs = ws.probs; a.edges = ws.edges; a.min_accept = ws.min_accept; a.sorted = ws.sorted;
+        a.base = ws.base; a.ctr = ws.d_ctr; a.binom = ws.binom; a.binom_rows = ws.brows;
+        a.d = d; a.gs = plain ? 1 : gs; a.smem_ints = (int)(kSmemBytes / 4); a.alpha = alpha;
+        a.gscratch = nullptr; a.gscratch_ints = 0;
+        const int grid = plain ? (int)std::min<long long>(E, fits_smem(max_cells) ? (1LL << 30) : pool_grid)
+                               : pool_grid;
+        if (!fits_smem(max_cells)) {
+            a.gscratch_ints = 3 * max_cells + 64;
+            rc = ensure_gscratch(h, ws, a.gscratch_ints * grid);
+            if (rc) return rc;
+            a.gscratch = ws.gscratch;
+        }
+        if (plain) {
+            CK(cudaEventRecord(ws.kev[0], st));
+            launch_plain(a, E, grid, kSmemBytes, st);
+            CK(cudaEventRecord(ws.kev[1], st));
+            launches += 1;
+        } else {
+            rc = ensure_order(h, ws, maxc);
+            if (rc) return rc;
+            a.base = ws.base;
+            launch_order(ws.edges, E, gs, maxc, ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.d_ctr, st);
+            CK(cudaEventRecord(ws.kev[0], st));
+            launch_pool(a, (unsigned long long)maxc, grid, kSmemBytes, st);
+            CK(cudaEventRecord(ws.kev[1], st));
+            launches += 4;
+        }
+        CK(cudaGetLastError());
+        launches += 1;   // k_apply
+        launch_apply(ws.probs, ws.edges, ws.min_accept, E, d, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr, st);
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ws.ev[d + 1], st));
+        CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        rc = check_status(h, ws.h_ctr->status);
+        if (rc) return rc;
+        float ms = 0.f, kms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ws.ev[d], ws.ev[d + 1]));
+        CK(cudaEventElapsedTime(&kms, ws.kev[0], ws.kev[1]));
+        stats.test_ms[d] = kms;
+        stats.depths = d + 1;
+        stats.edges[d] = E;
+        stats.tests[d] = (int64_t)ws.h_ctr->tests;
+        stats.tests_oracle[d] = (int64_t)ws.h_ctr->tests_oracle;
+        stats.removed[d] = (int64_t)ws.h_ctr->removed;
+        stats.ms[d] = ms;
+        sep_used = ws.h_ctr->sep_used;
+    }
+
+    stats.launches = launches;
+    // Bring the separating sets of every problem to the host.
+    std::vector<int32_t> pool(sep_used);
+    if (sep_used)
+        CK(cudaMemcpyAsync(pool.data(), ws.sep_pool, sep_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    for (int p = 0; p < k; ++p) {
+        fbn_handle* q = hs[p];
+        const size_t nn = (size_t)q->n * q->n;
+        std::vector<int32_t> len(nn);
+        std::vector<int64_t> off(nn);
+        CK(cudaMemcpyAsync(len.data(), q->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(off.data(), q->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        q->sep_len.assign(nn, -1);
+        q->sep_off.assign(nn, 0);
+        q->sep_members.clear();
+        for (int i = 0; i < q->n; ++i)
+            for (int j = i + 1; j < q->n; ++j) {
+                const size_t ij = (size_t)i * q->n + j;
+                const int32_t L = len[ij];
+                if (L < 0) continue;
+                q->sep_len[ij] = L;
+                q->sep_off[ij] = (int64_t)q->sep_members.size();
+                for (int t = 0; t < L; ++t) q->sep_members.push_back(pool[(size_t)off[ij] + t]);
+            }
+        q->stats = stats;
+        q->learnt = true;
+    }
+    return FBN_OK;
+}
+
+int copy_adj(fbn_handle* h, uint8_t* adj_out)
+{
+    if (!adj_out) return FBN_OK;
+    const size_t nn = (size_t)h->n * h->n;
+    CK(cudaMemcpyAsync(adj_out, h->d_adj, nn, cudaMemcpyDefault, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return FBN_OK;
+}
+
+int check_test_args(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, long long* cells)
+{
+    if (!h) return FBN_EINVAL;
+    if (x < 0 || x >= h->n || y < 0 || y >= h->n || x == y)
+        return fail(h, FBN_EINVAL, "bad x=%d y=%d for n=%d", x, y, h->n);
+    if (nz < 0 || nz > kMaxD || (nz > 0 && !z))
+        return fail(h, FBN_EINVAL, "conditioning set size %d outside [0, %d]", nz, kMaxD);
+    long long c = (long long)h->h_ar[x] * h->h_ar[y];
+    for (int k = 0; k < nz; ++k) {
+        if (z[k] < 0 || z[k] >= h->n || z[k] == x || z[k] == y)
+            return fail(h, FBN_EINVAL, "bad conditioning variable %d", z[k]);
+        for (int l = 0; l < k; ++l)
+            if (z[l] == z[k]) return fail(h, FBN_EINVAL, "conditioning variable %d repeated", z[k]);
+        c *= h->h_ar[z[k]];
+        if (c > kMaxCells) return fail(h, FBN_ETOOBIG, "table exceeds %lld cells", kMaxCells);
+    }
+    *cells = c;
+    return FBN_OK;
+}
+
+int run_ci(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, long long cells, bool want_table)
+{
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    CiTestDesc& q = *h->h_ci;
+    std::memset(&q, 0, sizeof q);
+    q.x = x; q.y = y; q.d = nz;
+    for (int k = 0; k < nz; ++k) q.z[k] = z[k];
+    if (want_table && cells > h->table_cap) {
+        dfree(h->d_table);
+        h->d_table = nullptr;
+        h->table_cap = 0;
+        CK(dalloc(&h->d_table, cells));
+        h->table_cap = cells;
+    }
+    long long gints = 0;
+    if (!fits_smem(cells)) {
+        gints = 3 * cells + 64;
+        if (gints > h->gscratch_ints) {
+            dfree(h->d_gscratch);
+            h->d_gscratch = nullptr;
+            h->gscratch_ints = 0;
+            CK(dalloc(&h->d_gscratch, gints));
+            h->gscratch_ints = gints;
+        }
+    }
+    CK(set_kernel_smem(kSmemBytes));
+    CK(cudaMemcpyAsync(h->d_ci, h->h_ci, sizeof(CiTestDesc), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
+    launch_ci_tests(h->d_prob, h->d_ci, 1, h->d_ci_out, want_table ? h->d_table : nullptr,
+                    gints ? h->d_gscratch : nullptr, gints, h->d_status, kSmemBytes, st);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_ci_out, h->d_ci_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return check_status(h, *h->h_status);
+}
+
+void free_handle(fbn_handle* h)
+{
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    h->ws.release();
+    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_deg);
+    dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
+    dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
+    if (h->h_ci) cudaFreeHost(h->h_ci);
+    if (h->h_ci_out) cudaFreeHost(h->h_ci_out);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+}  // namespace
+
+// ==========================================================================
+extern "C" {
+
+int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uint8_t* arities,
+               const fbn_options* opt, fbn_handle** out)
+{
+    fbn_handle* h = nullptr;
+    if (!out) return fail(nullptr, FBN_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!data || !arities) return fail(nullptr, FBN_EINVAL, "data or arities is NULL");
+    if (n_vars < 2) return fail(nullptr, FBN_EINVAL, "n_vars=%d < 2", n_vars);
+    if (n_samples < 1 || n_samples >= (1LL << 31)) return fail(nullptr, FBN_EINVAL, "n_samples=%lld outside [1, 2^31)", (long long)n_samples);
+    fbn_options o{};
+    o.device = -1;
+    if (opt) {
+        o = *opt;
+        for (int k = 0; k < 12; ++k)
+            if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
+        if (o.form != FBN_FORM_POOL && o.form != FBN_FORM_PLAIN) return fail(nullptr, FBN_EINVAL, "bad form %d", o.form);
+        if (o.group_size < 0) return fail(nullptr, FBN_EINVAL, "bad group_size %d", o.group_size);
+        if (o.depth0 < FBN_DEPTH0_AUTO || o.depth0 > FBN_DEPTH0_GRAM) return fail(nullptr, FBN_EINVAL, "bad depth0 %d", o.depth0);
+    }
+    int max_ar = 0;
+    for (int v = 0; v < n_vars; ++v) {
+        if (arities[v] < 2) return fail(nullptr, FBN_EINVAL, "arity of variable %d is %d < 2", v, arities[v]);
+        max_ar = std::max(max_ar, (int)arities[v]);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, FBN_ECUDA, "no CUDA device available");
+    }
+    int dev = o.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, FBN_ECUDA, "cudaGetDevice failed");
+    }
+    if (dev >= ndev) return fail(nullptr, FBN_EINVAL, "device %d of %d", dev, ndev);
+    if (cudaSetDevice(dev) != cudaSuccess) return fail(nullptr, FBN_ECUDA, "cudaSetDevice(%d) failed", dev);
+
+    h = new fbn_handle();
+    h->device = dev;
+    h->opt = o;
+    h->n = n_vars;
+    h->N = n_samples;
+    h->ld = (n_samples + 255) / 256 * 256;
+    h->max_arity = max_ar;
+    h->h_ar.assign(arities, arities + n_vars);
+    auto bail = [&](int code) {
+        std::string m = h->err;
+        free_handle(h);
+        g_create_error = m;
+        return code;
+    };
+#define CKC(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            fail(h, e_ == cudaErrorMemoryAllocation ? FBN_ENOMEM : FBN_ECUDA, "%s: %s", #call, \
+                 cudaGetErrorString(e_));                                                  \
+            return bail(e_ == cudaErrorMemoryAllocation ? FBN_ENOMEM : FBN_ECUDA);           \
+        }                                                                                  \
+    } while (0)
+    CKC(cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking));
+    h->stream = h->own_stream;
+    const size_t nn = (size_t)n_vars * n_vars;
+    CKC(dalloc(&h->d_data, (size_t)n_vars * h->ld));
+    CKC(dalloc(&h->d_ar, n_vars));
+    CKC(dalloc(&h->d_adj, nn));
+    CKC(dalloc(&h->d_nbr, nn));
+    CKC(dalloc(&h->d_deg, n_vars));
+    CKC(dalloc(&h->d_sep_len, nn));
+    CKC(dalloc(&h->d_sep_off, nn));
+    CKC(dalloc(&h->d_prob, 1));
+    CKC(dalloc(&h->d_ci, 1));
+    CKC(dalloc(&h->d_ci_out, 3));
+    CKC(dalloc(&h->d_status, 1));
+    CKC(cudaMallocHost((void**)&h->h_ci, sizeof(CiTestDesc)));
+    CKC(cudaMallocHost((void**)&h->h_ci_out, 3 * sizeof(double)));
+    CKC(cudaMallocHost((void**)&h->h_status, sizeof(unsigned long long)));
+    cudaStream_t st = h->stream;
+    CKC(cudaMemsetAsync(h->d_data, 0, (size_t)n_vars * h->ld, st));
+    CKC(cudaMemcpy2DAsync(h->d_data, h->ld, data, n_samples, n_samples, n_vars, cudaMemcpyDefault, st));
+    CKC(cudaMemcpyAsync(h->d_ar, arities, n_vars, cudaMemcpyHostToDevice, st));
+    // values must lie below their arity: checked on the device
+    unsigned long long* bad = (unsigned long long*)h->d_ci_out;   // scratch, 8 bytes
+    CKC(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st));
+    {
+        dim3 grid((unsigned)std::min<long long>((n_samples + 255) / 256, 64), n_vars);
+        k_validate<<<grid, 256, 0, st>>>(h->d_data, h->ld, n_vars, n_samples, h->d_ar, bad);
+    }
+    CKC(cudaGetLastError());
+    unsigned long long first_bad = 0;
+    CKC(cudaMemcpyAsync(h->h_status, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    std::memcpy(&first_bad, h->h_status, sizeof first_bad);
+    if (first_bad != ~0ULL) {
+        const long long v = (long long)(first_bad / (unsigned long long)n_samples);
+        const long long s = (long long)(first_bad % (unsigned long long)n_samples);
+        fail(h, FBN_EDATA, "value of variable %lld at sample %lld is >= its arity %d", v, s, (int)arities[v]);
+        return bail(FBN_EDATA);
+    }
+    ProblemDev P{};
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.deg = h->d_deg;
+    P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = n_vars; P.N = (int32_t)n_samples;
+    P.max_arity = max_ar;
+    CKC(cudaMemcpyAsync(h->d_prob, &P, sizeof P, cudaMemcpyHostToDevice, st));
+    CKC(cudaStreamSynchronize(st));
+#undef CKC
+    *out = h;
+    return FBN_OK;
+}
+
+int fbn_set_stream(fbn_handle* h, void* stream)
+{
+    if (!h) return FBN_EINVAL;
+    h->stream = stream ? (cudaStream_t)stream : h->own_stream;
+    return FBN_OK;
+}
+
+int fbn_ci_test(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, double* g2, double* df,
+                double* p)
+{
+    if (!h) return FBN_EINVAL;
+    if (!g2 || !df || !p) return fail(h, FBN_EINVAL, "null output pointer");
+    long long cells = 0;
+    int rc = check_test_args(h, x, y, z, nz, &cells);
+    if (rc) return rc;
+    rc = run_ci(h, x, y, z, nz, cells, false);
+    if (rc) return rc;
+    *g2 = h->h_ci_out[0];
+    *df = h->h_ci_out[1];
+    *p = h->h_ci_out[2];
+    return FBN_OK;
+}
+
+int fbn_ci_table(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, int32_t* counts, int64_t cap)
+{
+    if (!h) return FBN_EINVAL;
+    if (!counts) return fail(h, FBN_EINVAL, "counts is NULL");
+    long long cells = 0;
+    int rc = check_test_args(h, x, y, z, nz, &cells);
+    if (rc) return rc;
+    if (cap < cells) return fail(h, FBN_EINVAL, "cap %lld < %lld cells", (long long)cap, cells);
+    rc = run_ci(h, x, y, z, nz, cells, true);
+    if (rc) return rc;
+    CK(cudaMemcpy(counts, h->d_table, cells * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return FBN_OK;
+}
+
+int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* adj_out)
+{
+    if (!h) return FBN_EINVAL;
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
+    if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
+    h->learnt = false;
+    fbn_handle* hs[1] = {h};
+    int rc = run_skeleton(hs, 1, alpha, max_depth);
+    if (rc) return rc;
+    return copy_adj(h, adj_out);
+}
+
+int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth,
+                             uint8_t* const* adj_out)
+{
+    if (!hs || k < 1) return FBN_EINVAL;
+    fbn_handle* h = hs[0];
+    for (int p = 0; p < k; ++p) {
+        if (!hs[p]) return fail(h, FBN_EINVAL, "handle %d is NULL", p);
+        if (hs[p]->device != h->device) return fail(h, FBN_EINVAL, "handle %d is on another device", p);
+        hs[p]->learnt = false;
+    }
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
+    if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
+    int rc = run_skeleton(hs, k, alpha, max_depth);
+    if (rc) return rc;
+    if (adj_out)
+        for (int p = 0; p < k; ++p) {
+            if (!adj_out[p]) continue;
+            const size_t nn = (size_t)hs[p]->n * hs[p]->n;
+            CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, nn, cudaMemcpyDefault, h->stream));
+        }
+    CK(cudaStreamSynchronize(h->stream));
+    return FBN_OK;
+}
+
+int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, int32_t cap)
+{
+    if (!h || !h->learnt) return FBN_EINVAL;
+    if (i < 0 || j < 0 || i >= h->n || j >= h->n || i == j) return FBN_EINVAL;
+    if (i > j) std::swap(i, j);
+    const size_t ij = (size_t)i * h->n + j;
+    const int32_t L = h->sep_len[ij];
+    if (L < 0) return -1;
+    if (L > 0 && cap > 0 && !buf) return FBN_EINVAL;
+    for (int t = 0; t < L && t < cap; ++t) buf[t] = h->sep_members[(size_t)h->sep_off[ij] + t];
+    return L;
+}
+
+int fbn_export_sepsets(const fbn_handle* h, int64_t* n_removed, int64_t* n_members, int32_t* pairs,
+                       int64_t* offsets, int32_t* members)
+{
+    if (!h || !h->learnt || !n_removed || !n_members) return FBN_EINVAL;
+    int64_t nr = 0, nm = 0;
+    for (int i = 0; i < h->n; ++i)
+        for (int j = i + 1; j < h->n; ++j) {
+            const size_t ij = (size_t)i * h->n + j;
+            const int32_t L = h->sep_len[ij];
+            if (L < 0) continue;
+            if (pairs) { pairs[2 * nr] = i; pairs[2 * nr + 1] = j; }
+            if (offsets) offsets[nr] = nm;
+            if (members)
+                for (int t = 0; t < L; ++t) members[nm + t] = h->sep_members[(size_t)h->sep_off[ij] + t];
+            ++nr;
+            nm += L;
+        }
+    if (offsets) offsets[nr] = nm;
+    *n_removed = nr;
+    *n_members = nm;
+    return FBN_OK;
+}
+
+int fbn_get_stats(const fbn_handle* h, fbn_stats* out)
+{
+    if (!h || !out) return FBN_EINVAL;
+    *out = h->stats;
+    return FBN_OK;
+}
+
+const char* fbn_last_error(const fbn_handle* h)
+{
+    return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+void fbn_destroy(fbn_handle* h)
+{
+    free_handle(h);
+}
+
+}  // extern "C"

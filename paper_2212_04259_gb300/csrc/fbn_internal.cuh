@@ -1,0 +1,80 @@
+// fbn_internal.cuh -- device-side data structures shared by the kernels and the
+// host engine of the GB300 PC-stable skeleton library.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fbn {
+
+constexpr int kMaxD = 30;                 // largest conditioning set supported
+constexpr int kMaxRows = kMaxD + 2;       // S rows + X row + Y row
+constexpr int kBinomCols = kMaxD + 2;     // binomial table columns k = 0..kMaxD+1
+constexpr long long kBinomSat = 1LL << 62;
+constexpr long long kMaxCells = 1LL << 24;  // largest contingency table (cells)
+constexpr int kTestThreads = 256;         // threads of a test CTA
+constexpr int kTestWarps = kTestThreads / 32;
+
+// device status bits, OR-ed into DepthCounters::status
+constexpr unsigned kStatusTooBig = 1u;    // table over kMaxCells or scratch too small
+constexpr unsigned kStatusNumeric = 2u;   // p-value iteration hit its cap
+constexpr unsigned kStatusSepPool = 4u;   // separating-set pool overflow
+
+// One learning problem (one data set).  Arrays are device pointers.
+struct ProblemDev {
+    const uint8_t* data;   // [n][ld] uint8, variable-major, zero padded
+    const uint8_t* ar;     // [n] arities
+    uint8_t* adj;          // [n][n] current graph, 0/1
+    int32_t* nbr;          // [n][n] snapshot a(v), ascending, deg[v] valid entries
+    int32_t* deg;          // [n]
+    int32_t* sep_len;      // [n][n] (entry i<j), -1 while adjacent
+    int64_t* sep_off;      // [n][n] offset of the members in the shared pool
+    int64_t ld;            // row stride (bytes), multiple of 256
+    int32_t n;
+    int32_t N;
+    int32_t max_arity;
+    int32_t pad;
+};
+
+// One edge i<j of the current depth with its rank space: ranks [0, cnt_i) are
+// the X-side conditioning sets (subsets of a(i)\{j}), ranks [cnt_i, total) the
+// Y-side ones (subsets of a(j)\{i}), each side in lexicographic order.
+struct EdgeWork {
+    int32_t prob, i, j, pad;
+    int64_t cnt_i, total;
+};
+
+struct DepthCounters {
+    unsigned long long n_edges;       // edges appended by the edge-list kernel
+    unsigned long long maxc;          // largest chunk count of an edge
+    unsigned long long next_item;     // work-pool claim counter
+    unsigned long long total_items;   // work items of the depth
+    unsigned long long tests;         // CI tests executed
+    unsigned long long tests_oracle;  // tests of the sequential order (gs = 1)
+    unsigned long long removed;       // edges removed
+    unsigned long long sep_used;      // separating-set pool entries in use
+    unsigned long long max_cells;     // upper bound of table cells this depth
+    unsigned long long pad[6];
+    unsigned int status;
+    unsigned int pad2[3];
+};
+
+// Work pool of one depth.
+struct PoolArgs {
+    const ProblemDev* probs;
+    const EdgeWork* edges;
+    unsigned long long* min_accept;   // [E], lowest accepting rank, init = total
+    const int32_t* sorted;            // edges by chunk count, descending
+    const unsigned long long* base;   // [maxc + 1] first item of pass k
+    DepthCounters* ctr;
+    const long long* binom;           // [binom_rows][kBinomCols]
+    int* gscratch;                    // global tables, gscratch_ints per worker
+    long long gscratch_ints;
+    int32_t d;
+    int32_t gs;
+    int32_t smem_ints;
+    int32_t binom_rows;
+    double alpha;
+};
+
+}  // namespace fbn

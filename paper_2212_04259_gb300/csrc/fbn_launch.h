@@ -1,0 +1,37 @@
+// fbn_launch.h -- host-side launchers of the kernels in fbn_kernels.cu.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fbn_internal.cuh"
+
+namespace fbn {
+
+// One explicit CI test (fbn_ci_test / fbn_ci_table).
+struct CiTestDesc {
+    int32_t x, y, d, pad;
+    int32_t z[kMaxD];
+};
+
+void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
+                     int total_vertices, cudaStream_t st);
+void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
+                  int total_vertices, int d, int gs, const long long* binom, int brows, EdgeWork* edges,
+                  unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr, cudaStream_t st);
+void launch_order(const EdgeWork* edges, long long E, int gs, long long maxc, unsigned long long* hist,
+                  unsigned long long* alive, unsigned long long* base, unsigned long long* cursor,
+                  int32_t* sorted, DepthCounters* ctr, cudaStream_t st);
+void launch_pool(const PoolArgs& a, unsigned long long maxc, int grid, size_t smem_bytes, cudaStream_t st);
+void launch_plain(const PoolArgs& a, long long E, int grid, size_t smem_bytes, cudaStream_t st);
+void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
+                  long long E, int d, const long long* binom, int32_t* sep_pool, long long sep_cap,
+                  DepthCounters* ctr, cudaStream_t st);
+void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
+                     int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
+                     size_t smem_bytes, cudaStream_t st);
+cudaError_t set_kernel_smem(size_t smem_bytes);
+int pool_blocks_per_sm(size_t smem_bytes);
+
+}  // namespace fbn

@@ -1,0 +1,245 @@
+"""ctypes binding of libfbn (include/fbn.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to pointers, checks status codes and raises ``FbnError``.
+There is no CPU fallback: importing works without a GPU, but every call needs
+the built library and a CUDA device, and fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfbn.so")
+
+FBN_OK, FBN_EINVAL, FBN_EDATA, FBN_ENOMEM, FBN_ECUDA, FBN_ETOOBIG, FBN_ETIMEOUT, FBN_ENUMERIC = \
+    0, -1, -2, -3, -4, -5, -6, -7
+FORMS = {"pool": 0, "plain": 1}
+DEPTH0 = {"auto": 0, "hist": 1, "gram": 2}
+MAX_DEPTHS = 64
+
+# Every symbol include/fbn.h declares.
+EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
+           "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_get_stats",
+           "fbn_last_error", "fbn_destroy")
+
+
+class FbnError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"fbn error {code}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("form", C.c_int32), ("group_size", C.c_int32), ("depth0", C.c_int32),
+                ("device", C.c_int32), ("reserved", C.c_int32 * 12)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("depths", C.c_int32), ("reserved", C.c_int32), ("launches", C.c_int64),
+                ("edges", C.c_int64 * MAX_DEPTHS), ("tests", C.c_int64 * MAX_DEPTHS),
+                ("tests_oracle", C.c_int64 * MAX_DEPTHS), ("removed", C.c_int64 * MAX_DEPTHS),
+                ("ms", C.c_double * MAX_DEPTHS), ("test_ms", C.c_double * MAX_DEPTHS)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libfbn.so; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfbn.so is not built ({LIB_PATH}); run "
+                               "`python -m paper_2212_04259_gb300.build` (needs nvcc)")
+        L = C.CDLL(LIB_PATH)
+        p, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.fbn_create.restype = C.c_int
+        L.fbn_create.argtypes = [p, i32, i64, p, p, C.POINTER(p)]
+        L.fbn_set_stream.restype = C.c_int
+        L.fbn_set_stream.argtypes = [p, p]
+        L.fbn_ci_test.restype = C.c_int
+        L.fbn_ci_test.argtypes = [p, i32, i32, p, i32, p, p, p]
+        L.fbn_ci_table.restype = C.c_int
+        L.fbn_ci_table.argtypes = [p, i32, i32, p, i32, p, i64]
+        L.fbn_learn_skeleton.restype = C.c_int
+        L.fbn_learn_skeleton.argtypes = [p, f64, i32, p]
+        L.fbn_learn_skeleton_batch.restype = C.c_int
+        L.fbn_learn_skeleton_batch.argtypes = [p, i32, f64, i32, p]
+        L.fbn_get_sepset.restype = i32
+        L.fbn_get_sepset.argtypes = [p, i32, i32, p, i32]
+        L.fbn_export_sepsets.restype = C.c_int
+        L.fbn_export_sepsets.argtypes = [p, p, p, p, p, p]
+        L.fbn_get_stats.restype = C.c_int
+        L.fbn_get_stats.argtypes = [p, p]
+        L.fbn_last_error.restype = C.c_char_p
+        L.fbn_last_error.argtypes = [p]
+        L.fbn_destroy.restype = None
+        L.fbn_destroy.argtypes = [p]
+        _lib = L
+        return L
+
+
+def _check(rc, h=None):
+    if rc != FBN_OK:
+        msg = lib().fbn_last_error(h.ptr if h is not None else None)
+        raise FbnError(rc, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(x.data_ptr())
+
+
+class Handle:
+    """An fbn_handle*; destroyed on garbage collection or by fbn_destroy."""
+
+    def __init__(self, ptr, n, n_samples, arities):
+        self.ptr = ptr
+        self.n = n
+        self.n_samples = n_samples
+        self.arities = arities
+        self._keep = None
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            try:
+                lib().fbn_destroy(self.ptr)
+            except Exception:
+                pass
+            self.ptr = None
+
+
+def _as_u8_2d(data):
+    if isinstance(data, np.ndarray):
+        data = np.ascontiguousarray(data, dtype=np.uint8)
+        return data, data.shape
+    import torch  # torch tensors: host or device memory
+    if data.dtype != torch.uint8 or data.dim() != 2:
+        raise ValueError("data must be a 2-D uint8 tensor [n_vars][n_samples]")
+    data = data.contiguous()
+    return data, tuple(data.shape)
+
+
+def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-1) -> Handle:
+    """Upload variable-major uint8 data [n_vars][n_samples] (numpy, or torch host/device)."""
+    data, (n, N) = _as_u8_2d(data)
+    ar = np.ascontiguousarray(arities, dtype=np.uint8)
+    if ar.shape != (n,):
+        raise ValueError("arities must have one entry per variable")
+    o = Options(form=FORMS[form], group_size=group_size, depth0=DEPTH0[depth0], device=device)
+    out = C.c_void_p()
+    rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
+    _check(rc)
+    return Handle(out, n, N, ar.copy())
+
+
+def fbn_set_stream(h: Handle, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t (int) or None."""
+    if stream is None:
+        raw = None
+    elif isinstance(stream, int):
+        raw = stream
+    else:
+        raw = stream.cuda_stream
+    _check(lib().fbn_set_stream(h.ptr, C.c_void_p(raw) if raw else None), h)
+
+
+def _zarr(z):
+    return np.ascontiguousarray(list(z), dtype=np.int32)
+
+
+def fbn_ci_test(h: Handle, x: int, y: int, z=()):
+    """(G^2, df, p) of I(X, Y | Z)."""
+    za = _zarr(z)
+    g2, df, p = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().fbn_ci_test(h.ptr, x, y, _ptr(za) if len(za) else None, len(za), C.byref(g2),
+                             C.byref(df), C.byref(p)), h)
+    return g2.value, df.value, p.value
+
+
+def fbn_ci_table(h: Handle, x: int, y: int, z=(), cells=None) -> np.ndarray:
+    """Exact int32 contingency table, layout (zi * r_x + xv) * r_y + yv."""
+    za = _zarr(z)
+    if cells is None:
+        cells = int(h.arities[x]) * int(h.arities[y])
+        for v in za:
+            cells *= int(h.arities[v]) if 0 <= v < h.n else 1
+        cells = max(1, min(cells, 1 << 25))
+    out = np.zeros(cells, dtype=np.int32)
+    _check(lib().fbn_ci_table(h.ptr, x, y, _ptr(za) if len(za) else None, len(za), _ptr(out), cells), h)
+    return out
+
+
+def fbn_learn_skeleton(h: Handle, alpha: float, max_depth: int = -1, adj_out=None):
+    """Skeleton adjacency. adj_out: None (a numpy array is returned), or a
+    preallocated uint8 [n][n] numpy array / torch tensor (host or device)."""
+    out = np.zeros((h.n, h.n), dtype=np.uint8) if adj_out is None else adj_out
+    _check(lib().fbn_learn_skeleton(h.ptr, float(alpha), int(max_depth), _ptr(out)), h)
+    return out
+
+
+def fbn_learn_skeleton_batch(handles, alpha: float, max_depth: int = -1, adj_out=None):
+    k = len(handles)
+    arr = (C.c_void_p * k)(*[hh.ptr.value if isinstance(hh.ptr, C.c_void_p) else hh.ptr for hh in handles])
+    outs = [np.zeros((hh.n, hh.n), dtype=np.uint8) for hh in handles] if adj_out is None else adj_out
+    optr = (C.c_void_p * k)(*[_ptr(o).value for o in outs])
+    rc = lib().fbn_learn_skeleton_batch(C.cast(arr, C.c_void_p), k, float(alpha), int(max_depth),
+                                        C.cast(optr, C.c_void_p))
+    _check(rc, handles[0])
+    return outs
+
+
+def fbn_get_sepset(h: Handle, i: int, j: int):
+    """Separating set of (i, j) as a tuple, or None while adjacent."""
+    buf = np.zeros(64, dtype=np.int32)
+    k = lib().fbn_get_sepset(h.ptr, i, j, _ptr(buf), len(buf))
+    if k == -1:
+        return None
+    if k < -1:
+        _check(k, h)
+    return tuple(int(v) for v in buf[:k])
+
+
+def fbn_export_sepsets(h: Handle) -> dict:
+    """{(i, j): tuple(S)} for every removed pair i < j."""
+    nr, nm = C.c_int64(), C.c_int64()
+    L = lib()
+    _check(L.fbn_export_sepsets(h.ptr, C.byref(nr), C.byref(nm), None, None, None), h)
+    pairs = np.zeros((max(nr.value, 1), 2), dtype=np.int32)
+    offs = np.zeros(nr.value + 1, dtype=np.int64)
+    mem = np.zeros(max(nm.value, 1), dtype=np.int32)
+    _check(L.fbn_export_sepsets(h.ptr, C.byref(nr), C.byref(nm), _ptr(pairs), _ptr(offs), _ptr(mem)), h)
+    return {(int(pairs[k, 0]), int(pairs[k, 1])): tuple(int(v) for v in mem[offs[k]:offs[k + 1]])
+            for k in range(nr.value)}
+
+
+def fbn_get_stats(h: Handle) -> dict:
+    s = Stats()
+    _check(lib().fbn_get_stats(h.ptr, C.byref(s)), h)
+    d = s.depths
+    return {"depths": d, "launches": int(s.launches), "edges": list(s.edges[:d]),
+            "tests": list(s.tests[:d]), "tests_oracle": list(s.tests_oracle[:d]),
+            "removed": list(s.removed[:d]), "ms": list(s.ms[:d]), "test_ms": list(s.test_ms[:d])}
+
+
+def fbn_last_error(h: Handle | None = None) -> str:
+    m = lib().fbn_last_error(h.ptr if h is not None else None)
+    return m.decode() if m else ""
+
+
+def fbn_destroy(h: Handle) -> None:
+    if h.ptr:
+        lib().fbn_destroy(h.ptr)
+        h.ptr = None
