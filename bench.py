@@ -297,7 +297,7 @@ def main():
     except Exception:
         peak, peak_src = FALLBACK_HBM_GBS, "of fallback"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_src, "kernel": "k_pool" if args.form == "pool" else "k_plain",
+                "traffic": None, "peak_source": peak_src, "kernel": "k_pool<32>+k_pool<256>" if args.form == "pool" else "k_plain",
                 "kernel_ms_per_step": test_ms, "algorithmic_bytes_per_step": alg_bytes}
 
     # end to end through the public API with host buffers

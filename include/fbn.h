@@ -47,7 +47,8 @@ typedef struct fbn_options {
     int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default */
     int32_t depth0;      /* FBN_DEPTH0_* */
     int32_t device;      /* CUDA device ordinal; -1 = the current device */
-    int32_t reserved[12];/* must be zero */
+    int32_t group_threads; /* threads per CI test in the pool: 32, 64, 128 or 256; 0 = chosen per depth */
+    int32_t reserved[11];/* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */

@@ -20,8 +20,10 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr size_t kSmemBytes = 108 * 1024;   // dynamic shared memory of a test CTA (2 CTAs / SM)
+constexpr size_t kSmemBytes = 108 * 1024;     // dynamic shared memory of a CTA test group (2 CTAs / SM)
+constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
 constexpr int kDefaultGs = 4;
+constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
@@ -85,6 +87,9 @@ struct Workspace {
     long long sep_cap = 0;
     int* gscratch = nullptr;
     long long gscratch_total = 0;
+    long long* crit_keys = nullptr;
+    double* crit_vals = nullptr;
+    double crit_alpha = -1.0;
     cudaEvent_t ev[FBN_MAX_DEPTHS + 1] = {};
     cudaEvent_t kev[2] = {};
     bool events = false;
@@ -96,7 +101,7 @@ struct Workspace {
         dfree(d_ctr);
         if (h_ctr) cudaFreeHost(h_ctr);
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
-        dfree(sep_pool); dfree(gscratch);
+        dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals);
         if (events) {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
@@ -182,6 +187,8 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         for (auto& e : ws.ev) CK(cudaEventCreate(&e));
         for (auto& e : ws.kev) CK(cudaEventCreate(&e));
         ws.events = true;
+        CK(dalloc(&ws.crit_keys, kCritCap));
+        CK(dalloc(&ws.crit_vals, kCritCap));
     }
     if (edge_cap > ws.edge_cap) {
         dfree(ws.edges); dfree(ws.min_accept); dfree(ws.sorted);
@@ -268,12 +275,18 @@ int ensure_gscratch(fbn_handle* h, Workspace& ws, long long total_ints)
     return FBN_OK;
 }
 
-// Shared-memory ints a test CTA can use for counts of a table of C cells
-// without falling back to a global table.
-bool fits_smem(long long C)
+// Whether a table of C cells (plus its marginals, at most 1.25 C entries as
+// r_x, r_y >= 2) fits a shared-memory budget without a global table.
+bool fits_smem(long long C, size_t bytes = kSmemBytes)
 {
-    const long long budget = (long long)(kSmemBytes / 4);
-    return C + (C * 5) / 4 + 8 <= budget;   // table + marginals bound (r_x, r_y >= 2)
+    return C + (C * 5) / 4 + 8 <= (long long)(bytes / 4);
+}
+
+// Largest table a warp group takes: its eighth of the CTA's shared memory.
+long long warp_cells_cap()
+{
+    const long long slice = (long long)(kWarpSmemBytes / 4) / (kTestThreads / 32);
+    return (slice - 8) * 4 / 9;   // C + 1.25 C <= slice - 8
 }
 
 int check_status(fbn_handle* h, unsigned status)
@@ -281,6 +294,7 @@ int check_status(fbn_handle* h, unsigned status)
     if (status & kStatusTooBig) return fail(h, FBN_ETOOBIG, "a contingency table exceeds %lld cells", kMaxCells);
     if (status & kStatusNumeric) return fail(h, FBN_ENUMERIC, "p-value iteration did not converge");
     if (status & kStatusSepPool) return fail(h, FBN_ECUDA, "separating-set pool overflow");
+    if (status & kStatusEdges) return fail(h, FBN_ECUDA, "edge list overflow");
     return FBN_OK;
 }
 
@@ -319,10 +333,19 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
     int dev_sms = 0;
     CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
     CK(set_kernel_smem(kSmemBytes));
-    const int bps = std::max(1, pool_blocks_per_sm(kSmemBytes));
-    const int pool_grid = dev_sms * bps;
+    // CTAs per SM of each group size on the small-table configuration, and of
+    // CTA groups on the big-table one
+    const int gsizes[4] = {32, 64, 128, kTestThreads};
+    int grid_small[4];
+    for (int k = 0; k < 4; ++k) grid_small[k] = dev_sms * std::max(1, pool_blocks_per_sm(gsizes[k], kWarpSmemBytes));
+    const int grid_big = dev_sms * std::max(1, pool_blocks_per_sm(kTestThreads, kSmemBytes));
     const int gs = h->opt.group_size > 0 ? h->opt.group_size : kDefaultGs;
     const bool plain = h->opt.form == FBN_FORM_PLAIN;
+    const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
+    if (ws.crit_alpha != alpha) {
+        CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
+        ws.crit_alpha = alpha;
+    }
 
     fbn_stats stats{};
     unsigned long long sep_used = 0;
@@ -336,52 +359,101 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
         CK(cudaEventRecord(ws.ev[d], st));
         CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st);
-        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, d, plain ? 1 : gs, ws.binom, ws.brows,
+        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, d, plain ? 1 : gs, ws.binom, ws.brows, wcap,
                      ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, st);
         CK(cudaGetLastError());
         launches += 2;
         CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        const long long E = (long long)ws.h_ctr->n_edges;
+        rc = check_status(h, ws.h_ctr->status);
+        if (rc) return rc;
+        const long long Ec[2] = {(long long)ws.h_ctr->n_edges[0], (long long)ws.h_ctr->n_edges[1]};
+        const long long E = Ec[0] + Ec[1];
         if (E == 0) break;   // no edge has a side with >= d candidates (Algorithm 1, last line)
-        const long long maxc = (long long)ws.h_ctr->maxc;
-        const long long max_cells = (long long)ws.h_ctr->max_cells;
-        if (max_cells > kMaxCells)
+        const long long maxc[2] = {(long long)ws.h_ctr->maxc[0], (long long)ws.h_ctr->maxc[1]};
+        const long long mcells[2] = {(long long)ws.h_ctr->max_cells[0], (long long)ws.h_ctr->max_cells[1]};
+        if (mcells[1] > kMaxCells)
             return fail(h, FBN_ETOOBIG, "depth %d may need tables of more than %lld cells", d, kMaxCells);
         rc = ensure_sep_pool(h, ws, (long long)sep_used + E * d + 1, (long long)sep_used, st);
         if (rc) return rc;
 
-        PoolArgs a{};
-        a.probs = ws.probs; a.edges = ws.edges; a.min_accept = ws.min_accept; a.sorted = ws.sorted;
-        a.base = ws.base; a.ctr = ws.d_ctr; a.binom = ws.binom; a.binom_rows = ws.brows;
-        a.d = d; a.gs = plain ? 1 : gs; a.smem_ints = (int)(kSmemBytes / 4); a.alpha = alpha;
-        a.gscratch = nullptr; a.gscratch_ints = 0;
-        const int grid = plain ? (int)std::min<long long>(E, fits_smem(max_cells) ? (1LL << 30) : pool_grid)
-                               : pool_grid;
-        if (!fits_smem(max_cells)) {
-            a.gscratch_ints = 3 * max_cells + 64;
-            rc = ensure_gscratch(h, ws, a.gscratch_ints * grid);
-            if (rc) return rc;
-            a.gscratch = ws.gscratch;
+        CK(cudaEventRecord(ws.kev[0], st));
+        int group_used[2] = {0, 0};
+        for (int cls = 0; cls < 2; ++cls) {
+            if (Ec[cls] == 0) continue;
+            const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
+            PoolArgs a{};
+            a.probs = ws.probs;
+            a.edges = ws.edges + off;
+            a.min_accept = ws.min_accept + off;
+            a.sorted = ws.sorted;
+            a.next_item = &ws.d_ctr->next_item[cls];
+            a.total_items = &ws.d_ctr->total_items[cls];
+            a.tests = &ws.d_ctr->tests;
+            a.status = &ws.d_ctr->status;
+            a.binom = ws.binom;
+            a.binom_rows = ws.brows;
+            a.crit.keys = ws.crit_keys;
+            a.crit.vals = ws.crit_vals;
+            a.crit.cap = kCritCap;
+            a.maxc = maxc[cls];
+            a.d = d;
+            a.gs = plain ? 1 : gs;
+            a.alpha = alpha;
+            const bool warp_cls = cls == kClassWarp && !plain;
+            const size_t smem = warp_cls ? kWarpSmemBytes : kSmemBytes;
+            a.smem_ints = (int)(smem / 4);
+            // group size: the smallest whose group count the edges still fill
+            // twice over (more groups hide latency; bigger groups finish a test
+            // sooner when there are few of them)
+            int group = kTestThreads, grid = grid_big;
+            if (warp_cls) {
+                group = kTestThreads;
+                grid = grid_small[3];
+                for (int k = 0; k < 3; ++k) {
+                    const long long groups = (long long)grid_small[k] * (kTestThreads / gsizes[k]);
+                    if (Ec[cls] >= 2 * groups) {
+                        group = gsizes[k];
+                        grid = grid_small[k];
+                        break;
+                    }
+                }
+            }
+            if (warp_cls && h->opt.group_threads) {
+                group = h->opt.group_threads;
+                for (int k = 0; k < 4; ++k)
+                    if (gsizes[k] == group) grid = grid_small[k];
+            }
+            if (plain) grid = (int)std::min<long long>(Ec[cls], fits_smem(mcells[cls]) ? (1LL << 30) : grid_big);
+            group_used[cls] = group;
+            if (!warp_cls && !fits_smem(mcells[cls])) {
+                a.gscratch_ints = 3 * mcells[cls] + 64;
+                rc = ensure_gscratch(h, ws, a.gscratch_ints * grid);
+                if (rc) return rc;
+                a.gscratch = ws.gscratch;
+            }
+            if (plain) {
+                launch_plain(a, Ec[cls], grid, kSmemBytes, st);
+                launches += 1;
+            } else {
+                rc = ensure_order(h, ws, maxc[cls]);
+                if (rc) return rc;
+                a.base = ws.base;
+                launch_order(a.edges, Ec[cls], gs, maxc[cls], ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted,
+                             &ws.d_ctr->total_items[cls], &ws.d_ctr->next_item[cls], st);
+                launch_pool(a, group, grid, smem, st);
+                launches += 4;
+            }
+            CK(cudaGetLastError());
         }
-        if (plain) {
-            CK(cudaEventRecord(ws.kev[0], st));
-            launch_plain(a, E, grid, kSmemBytes, st);
-            CK(cudaEventRecord(ws.kev[1], st));
+        CK(cudaEventRecord(ws.kev[1], st));
+        for (int cls = 0; cls < 2; ++cls) {
+            if (Ec[cls] == 0) continue;
+            const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
+            launch_apply(ws.probs, ws.edges + off, ws.min_accept + off, Ec[cls], d, ws.binom, ws.sep_pool,
+                         ws.sep_cap, ws.d_ctr, st);
             launches += 1;
-        } else {
-            rc = ensure_order(h, ws, maxc);
-            if (rc) return rc;
-            a.base = ws.base;
-            launch_order(ws.edges, E, gs, maxc, ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.d_ctr, st);
-            CK(cudaEventRecord(ws.kev[0], st));
-            launch_pool(a, (unsigned long long)maxc, grid, kSmemBytes, st);
-            CK(cudaEventRecord(ws.kev[1], st));
-            launches += 4;
         }
-        CK(cudaGetLastError());
-        launches += 1;   // k_apply
-        launch_apply(ws.probs, ws.edges, ws.min_accept, E, d, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr, st);
         CK(cudaGetLastError());
         CK(cudaEventRecord(ws.ev[d + 1], st));
         CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
@@ -527,14 +599,18 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     if (!out) return fail(nullptr, FBN_EINVAL, "out is NULL");
     *out = nullptr;
     if (!data || !arities) return fail(nullptr, FBN_EINVAL, "data or arities is NULL");
-    if (n_vars < 2) return fail(nullptr, FBN_EINVAL, "n_vars=%d < 2", n_vars);
+    if (n_vars < 2 || n_vars > kMaxVars)
+        return fail(nullptr, FBN_EINVAL, "n_vars=%d outside [2, %d]", n_vars, kMaxVars);
     if (n_samples < 1 || n_samples >= (1LL << 31)) return fail(nullptr, FBN_EINVAL, "n_samples=%lld outside [1, 2^31)", (long long)n_samples);
     fbn_options o{};
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 12; ++k)
+        for (int k = 0; k < 11; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
+        if (o.group_threads != 0 && o.group_threads != 32 && o.group_threads != 64 && o.group_threads != 128 &&
+            o.group_threads != kTestThreads)
+            return fail(nullptr, FBN_EINVAL, "bad group_threads %d", o.group_threads);
         if (o.form != FBN_FORM_POOL && o.form != FBN_FORM_PLAIN) return fail(nullptr, FBN_EINVAL, "bad form %d", o.form);
         if (o.group_size < 0) return fail(nullptr, FBN_EINVAL, "bad group_size %d", o.group_size);
         if (o.depth0 < FBN_DEPTH0_AUTO || o.depth0 > FBN_DEPTH0_GRAM) return fail(nullptr, FBN_EINVAL, "bad depth0 %d", o.depth0);

@@ -1,6 +1,12 @@
-// fbn_device.cuh -- CTA-level conditional-independence test for sm_103a:
-// contingency counts over all samples, marginals, G^2 (FP64 terms) and the
-// chi-square p-value, plus the lexicographic unranking of conditioning sets.
+// fbn_device.cuh -- group-level conditional-independence test for sm_103a:
+// contingency counts over all samples, marginals, G^2 and the decision
+// against alpha, plus the lexicographic unranking of conditioning sets.
+//
+// A "group" is the set of threads that runs one test: one warp (G = 32) or a
+// whole CTA (G = kTestThreads).  Warp groups let many small tests run
+// concurrently on an SM so that the latency of one test's setup and epilogue
+// is hidden by the others; CTA groups serve tables too big for a warp's share
+// of shared memory.
 #pragma once
 
 #include <cstdint>
@@ -54,13 +60,80 @@ __device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status
     return q > 1.0 ? 1.0 : q;
 }
 
+// Critical value of the test: the G^2 at which Q(df/2, G^2/2) = alpha.  Q is
+// strictly decreasing in G^2, so "p > alpha" is exactly "G^2 < crit".  Found
+// by a safeguarded Newton iteration inside a bracket [lo, hi] with Q(lo) >
+// alpha >= Q(hi); the derivative of Q in G^2 is minus the chi-square density.
+__device__ __forceinline__ double chisq_crit(double df, double alpha, unsigned* status)
+{
+    const double a = 0.5 * df;
+    double lo = 0.0, hi = df + 10.0 * sqrt(2.0 * df) + 40.0;
+    for (int k = 0; k < 64 && chisq_q(df, hi, status) > alpha; ++k) {
+        lo = hi;
+        hi *= 2.0;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 200; ++it) {
+        const double q = chisq_q(df, x, status);
+        if (q > alpha) lo = x; else hi = x;
+        // density of chi^2_df at x: x^{a-1} e^{-x/2} / (2^a Gamma(a))
+        const double lpdf = (a - 1.0) * log(x) - 0.5 * x - a * 0.6931471805599453 - lgamma(a);
+        const double pdf = exp(lpdf);
+        double nx = pdf > 0.0 ? x + (q - alpha) / pdf : 0.5 * (lo + hi);
+        if (!(nx > lo && nx < hi)) nx = 0.5 * (lo + hi);
+        if (fabs(nx - x) <= 1e-15 * x || hi - lo <= 1e-15 * hi) {
+            x = nx;
+            break;
+        }
+        x = nx;
+    }
+    return x;
+}
+
+// Open-addressing cache of critical values keyed by df (for one alpha).  A
+// slot is claimed with a CAS to -1, filled, then published with a release
+// store of the key; readers that see -1 compute the value themselves, so no
+// thread ever waits on another.
+using CritTable = CritTableDev;
+
+__device__ __forceinline__ long long ld_acquire(const long long* p)
+{
+    long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(long long* p, long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ double crit_get(const CritTable& t, long long df, double alpha, unsigned* status)
+{
+    unsigned h = (unsigned)(df * 0x9E3779B97F4A7C15ULL >> 40) & (unsigned)(t.cap - 1);
+    for (int probe = 0; probe < 32; ++probe, h = (h + 1) & (unsigned)(t.cap - 1)) {
+        const long long k = ld_acquire(t.keys + h);
+        if (k == df) return t.vals[h];
+        if (k == 0) {
+            const double c = chisq_crit((double)df, alpha, status);
+            if (atomicCAS((unsigned long long*)(t.keys + h), 0ULL, (unsigned long long)-1LL) == 0ULL) {
+                t.vals[h] = c;
+                st_release(t.keys + h, df);
+            }
+            return c;
+        }
+        if (k == -1) return chisq_crit((double)df, alpha, status);
+    }
+    return chisq_crit((double)df, alpha, status);
+}
+
 // --------------------------------------------------------------------------
 // Conditioning sets on the fly (Section IV-C): the r-th q-subset of {0..p-1}
 // in lexicographic order, from a table of binomials B[n][k] = C(n, k).
 __device__ __forceinline__ long long binom_at(const long long* B, int n, int k)
 {
     if (k < 0 || n < k) return 0;
-    return B[(long long)n * kBinomCols + k];
+    return __ldg(B + (long long)n * kBinomCols + k);
 }
 
 __device__ __forceinline__ void unrank_lex(long long r, int p, int q, const long long* B, int* out)
@@ -93,7 +166,7 @@ __device__ __forceinline__ bool next_subset(int p, int q, int* c)
 }
 
 // --------------------------------------------------------------------------
-// One CI test, described in shared memory by the CTA's leader.
+// One CI test as seen by its group, in shared memory.
 // rows = [S_0 .. S_{d-1}, X, Y]; the cell of a sample is the mixed-radix
 // number of its values in that order: ((z * r_x + x) * r_y + y).
 struct TestSpec {
@@ -102,216 +175,323 @@ struct TestSpec {
     int nrows;        // d + 2
     int rx, ry;
     int N;
-    long long cells;  // prod of all radices
+    long long cells;  // product of all radices
 };
 
-struct TestResult {
-    double g2, df, p;
+template <int G>
+struct Grp {
+    static_assert(G == 32 || G == 64 || G == 128 || G == kTestThreads, "group size");
+    static constexpr int kWarps = G / 32;
+    static __device__ __forceinline__ int rank() { return (int)(threadIdx.x % G); }
+    static __device__ __forceinline__ int gid() { return (int)(threadIdx.x / G); }
+    static __device__ __forceinline__ void sync()
+    {
+        if (G == 32) {
+            __syncwarp();
+        } else if (G == kTestThreads) {
+            __syncthreads();
+        } else {   // named barrier 1 + group index, G threads
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + gid()), "r"(G) : "memory");
+        }
+    }
 };
 
-enum CountMode { kLane = 0, kWarp = 1, kCta = 2, kGlobal = 3 };
-
-__device__ __forceinline__ unsigned byte_of(const uint4& w, int b)
+// Sum over the group; every thread of the group gets the total.  red: the
+// CTA's scratch of 32 entries, of which the group uses kWarps.
+template <int G, typename T>
+__device__ __forceinline__ T grp_sum(T v, T* red)
 {
-    const unsigned word = (b < 4) ? w.x : (b < 8) ? w.y : (b < 12) ? w.z : w.w;
-    return (word >> ((b & 3) * 8)) & 0xFFu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (G == 32) return v;
+    T* r = red + Grp<G>::gid() * Grp<G>::kWarps;
+    Grp<G>::sync();
+    if ((threadIdx.x & 31) == 0) r[Grp<G>::rank() >> 5] = v;
+    Grp<G>::sync();
+    T t = 0;
+#pragma unroll
+    for (int w = 0; w < Grp<G>::kWarps; ++w) t += r[w];
+    return t;
 }
+
+enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3 };
 
 template <int MODE>
 __device__ __forceinline__ void bump(int* base, unsigned idx)
 {
-    if (MODE == kLane) base[idx * 32u] += 1;        // lane-private column: no race, no atomic
+    if (MODE == kLane) base[idx * 32u] += 1;        // this lane's private column: no race, no atomic
     else atomicAdd(base + idx, 1);
 }
 
-// Count 16-sample vectors (16-byte loads of every row) plus the ragged tail.
-// NR > 0: number of rows known at compile time; NR == 0: runtime s.nrows.
-template <int NR, int MODE>
-__device__ __forceinline__ void count_samples(const TestSpec& s, int* base)
+// Count 16-sample vectors (one 16-byte load per row) plus the ragged tail.
+// The cell index of two samples is carried in the two 16-bit halves of one
+// 32-bit register (every partial index is below cells <= 65536), so one IMAD
+// advances two samples.  NR > 0: rows known at compile time; NR == 0: runtime.
+template <int NR>
+__device__ __forceinline__ void pack_vector(const TestSpec& s, const uint4* w, unsigned* acc)
 {
-    const int nvec = s.N >> 4;
-    if (NR > 0) {
-        const uint4* r[NR > 0 ? NR : 1];
-        unsigned rad[NR > 0 ? NR : 1];
+    {
+        const unsigned ws[4] = {w[0].x, w[0].y, w[0].z, w[0].w};
 #pragma unroll
-        for (int k = 0; k < NR; ++k) {
-            r[k] = reinterpret_cast<const uint4*>(s.rows[k]);
-            rad[k] = (unsigned)s.rad[k];
-        }
-        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-            uint4 w[NR > 0 ? NR : 1];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) w[k] = __ldg(r[k] + v);
-            unsigned idx[16];
-#pragma unroll
-            for (int b = 0; b < 16; ++b) idx[b] = byte_of(w[0], b);
-#pragma unroll
-            for (int k = 1; k < NR; ++k)
-#pragma unroll
-                for (int b = 0; b < 16; ++b) idx[b] = idx[b] * rad[k] + byte_of(w[k], b);
-#pragma unroll
-            for (int b = 0; b < 16; ++b) bump<MODE>(base, idx[b]);
-        }
-    } else {
-        const int nr = s.nrows;
-        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-            uint4 w = __ldg(reinterpret_cast<const uint4*>(s.rows[0]) + v);
-            unsigned idx[16];
-#pragma unroll
-            for (int b = 0; b < 16; ++b) idx[b] = byte_of(w, b);
-            for (int k = 1; k < nr; ++k) {
-                w = __ldg(reinterpret_cast<const uint4*>(s.rows[k]) + v);
-                const unsigned rk = (unsigned)s.rad[k];
-#pragma unroll
-                for (int b = 0; b < 16; ++b) idx[b] = idx[b] * rk + byte_of(w, b);
-            }
-#pragma unroll
-            for (int b = 0; b < 16; ++b) bump<MODE>(base, idx[b]);
+        for (int q = 0; q < 4; ++q) {
+            acc[2 * q] = __byte_perm(ws[q], 0u, 0x4140);      // bytes 0,1 -> halves
+            acc[2 * q + 1] = __byte_perm(ws[q], 0u, 0x4342);  // bytes 2,3 -> halves
         }
     }
-    for (int t = (nvec << 4) + threadIdx.x; t < s.N; t += blockDim.x) {
+#pragma unroll
+    for (int k = 1; k < NR; ++k) {
+        const unsigned rk = (unsigned)s.rad[k];
+        const unsigned ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            acc[2 * q] = acc[2 * q] * rk + __byte_perm(ws[q], 0u, 0x4140);
+            acc[2 * q + 1] = acc[2 * q + 1] * rk + __byte_perm(ws[q], 0u, 0x4342);
+        }
+    }
+}
+
+template <int MODE>
+__device__ __forceinline__ void bump_packed(int* base, const unsigned* acc)
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        bump<MODE>(base, acc[q] & 0xFFFFu);
+        bump<MODE>(base, acc[q] >> 16);
+    }
+}
+
+// Count 16-sample vectors (one 16-byte load per row) plus the ragged tail.
+// The cell index of two samples is carried in the two 16-bit halves of one
+// 32-bit register (every partial index is below cells <= 65536), so one IMAD
+// advances two samples.  Two vectors are loaded before either is counted, to
+// keep 2 (d + 2) loads in flight per thread.  NR > 0: rows known at compile
+// time; NR == 0: runtime.
+template <int G, int NR, int MODE>
+__device__ __forceinline__ void count_packed(const TestSpec& s, int* base)
+{
+    const int nvec = s.N >> 4;
+    const int t0 = Grp<G>::rank();
+    const int nr = NR > 0 ? NR : s.nrows;
+    if (NR > 0) {
+        const uint4* r[NR > 0 ? NR : 1];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) r[k] = reinterpret_cast<const uint4*>(s.rows[k]);
+        int v = t0;
+        for (; v + G < nvec; v += 2 * G) {
+            uint4 w0[NR > 0 ? NR : 1], w1[NR > 0 ? NR : 1];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                w0[k] = __ldg(r[k] + v);
+                w1[k] = __ldg(r[k] + v + G);
+            }
+            unsigned acc[8];
+            pack_vector<NR>(s, w0, acc);
+            bump_packed<MODE>(base, acc);
+            pack_vector<NR>(s, w1, acc);
+            bump_packed<MODE>(base, acc);
+        }
+        if (v < nvec) {
+            uint4 w0[NR > 0 ? NR : 1];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) w0[k] = __ldg(r[k] + v);
+            unsigned acc[8];
+            pack_vector<NR>(s, w0, acc);
+            bump_packed<MODE>(base, acc);
+        }
+    } else {
+        for (int v = t0; v < nvec; v += G) {
+            unsigned acc[8];
+            {
+                const uint4 w = __ldg(reinterpret_cast<const uint4*>(s.rows[0]) + v);
+                const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[2 * q] = __byte_perm(ws[q], 0u, 0x4140);
+                    acc[2 * q + 1] = __byte_perm(ws[q], 0u, 0x4342);
+                }
+            }
+            for (int k = 1; k < nr; ++k) {
+                const uint4 w = __ldg(reinterpret_cast<const uint4*>(s.rows[k]) + v);
+                const unsigned rk = (unsigned)s.rad[k];
+                const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[2 * q] = acc[2 * q] * rk + __byte_perm(ws[q], 0u, 0x4140);
+                    acc[2 * q + 1] = acc[2 * q + 1] * rk + __byte_perm(ws[q], 0u, 0x4342);
+                }
+            }
+            bump_packed<MODE>(base, acc);
+        }
+    }
+    for (int t = (nvec << 4) + t0; t < s.N; t += G) {
+        unsigned idx = s.rows[0][t];
+        for (int k = 1; k < nr; ++k) idx = idx * (unsigned)s.rad[k] + s.rows[k][t];
+        bump<MODE>(base, idx);
+    }
+}
+
+// Same, one sample per 32-bit index (tables above 65536 cells).
+template <int G, int MODE>
+__device__ __forceinline__ void count_wide(const TestSpec& s, int* base)
+{
+    const int nvec = s.N >> 4;
+    const int t0 = Grp<G>::rank();
+    for (int v = t0; v < nvec; v += G) {
+        unsigned idx[16];
+        {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(s.rows[0]) + v);
+            const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int b = 0; b < 16; ++b) idx[b] = (ws[b >> 2] >> ((b & 3) * 8)) & 0xFFu;
+        }
+        for (int k = 1; k < s.nrows; ++k) {
+            const uint4 w = __ldg(reinterpret_cast<const uint4*>(s.rows[k]) + v);
+            const unsigned rk = (unsigned)s.rad[k];
+            const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int b = 0; b < 16; ++b) idx[b] = idx[b] * rk + ((ws[b >> 2] >> ((b & 3) * 8)) & 0xFFu);
+        }
+#pragma unroll
+        for (int b = 0; b < 16; ++b) bump<MODE>(base, idx[b]);
+    }
+    for (int t = (nvec << 4) + t0; t < s.N; t += G) {
         unsigned idx = s.rows[0][t];
         for (int k = 1; k < s.nrows; ++k) idx = idx * (unsigned)s.rad[k] + s.rows[k][t];
         bump<MODE>(base, idx);
     }
 }
 
-template <int MODE>
+template <int G, int MODE>
 __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 {
+    if (s.cells > 65536) {
+        count_wide<G, MODE>(s, base);
+        return;
+    }
     switch (s.nrows) {
-        case 2: count_samples<2, MODE>(s, base); break;
-        case 3: count_samples<3, MODE>(s, base); break;
-        case 4: count_samples<4, MODE>(s, base); break;
-        case 5: count_samples<5, MODE>(s, base); break;
-        case 6: count_samples<6, MODE>(s, base); break;
-        default: count_samples<0, MODE>(s, base); break;
+        case 2: count_packed<G, 2, MODE>(s, base); break;
+        case 3: count_packed<G, 3, MODE>(s, base); break;
+        case 4: count_packed<G, 4, MODE>(s, base); break;
+        case 5: count_packed<G, 5, MODE>(s, base); break;
+        case 6: count_packed<G, 6, MODE>(s, base); break;
+        default: count_packed<G, 0, MODE>(s, base); break;
     }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red)
+// Shared-memory ints needed by each counting strategy for a table of C cells
+// (marg = marginal entries); kGlobal when none fits.
+template <int G>
+__device__ __forceinline__ int pick_mode(long long C, long long marg, long long slice_ints)
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        t = lane < nw ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread 0
-}
-
-// Pick the counting strategy from the table size and the shared-memory budget.
-__device__ __forceinline__ int pick_mode(long long C, long long marg, int smem_ints, int nwarps)
-{
-    if (C * 32 * nwarps + C + marg <= smem_ints) return kLane;
-    if (C * nwarps + marg <= smem_ints) return kWarp;
-    if (C + marg <= smem_ints) return kCta;
+    if (C * G + C + marg <= slice_ints) return kLane;
+    if (Grp<G>::kWarps > 1 && C * Grp<G>::kWarps + marg <= slice_ints) return kWarp;
+    if (C + marg <= slice_ints) return kShared;
     return kGlobal;
 }
 
-// The whole test, run by every thread of the CTA.  smem: smem_ints ints of
-// dynamic shared memory; gtab: this CTA's global scratch (gtab_ints ints) for
-// tables that do not fit; table_out: optional copy of the final counts.
-// Returns the result in thread 0 (and writes it to *res when non-null).
-__device__ TestResult run_test(const TestSpec& s, int* smem, int smem_ints, int* gtab,
-                               long long gtab_ints, int32_t* table_out, unsigned* status,
-                               double* red)
+// Count the table of the test and merge private copies.  Returns the merged
+// table T and sets *M to the space for the marginals; returns nullptr when the
+// table fits neither the slice nor the global scratch.
+template <int G>
+__device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, int* gtab, long long gtab_ints,
+                          int** M)
 {
     const long long C = s.cells;
-    const int rxy = s.rx * s.ry;
-    const long long nz = C / rxy;
+    const long long nz = C / (s.rx * s.ry);
     const long long marg = nz * (s.rx + s.ry + 1);
-    const int nw = blockDim.x >> 5;
-    int mode = pick_mode(C, marg, smem_ints, nw);
-    if (mode == kGlobal && C + marg > gtab_ints) {
-        if (threadIdx.x == 0) atomicOr(status, kStatusTooBig);
-        TestResult bad = {0.0, 0.0, 0.0};
-        return bad;
-    }
-    int* cnt;
-    long long zero_n;
-    if (mode == kLane) { cnt = smem; zero_n = C * 32 * nw; }
-    else if (mode == kWarp) { cnt = smem; zero_n = C * nw; }
-    else if (mode == kCta) { cnt = smem; zero_n = C; }
-    else { cnt = gtab; zero_n = C; }
-    for (long long k = threadIdx.x; k < zero_n; k += blockDim.x) cnt[k] = 0;
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int mode = pick_mode<G>(C, marg, slice_ints);
+    if (mode == kGlobal && (gtab == nullptr || C + marg > gtab_ints)) return nullptr;
+    const int r = Grp<G>::rank();
+    const int lane = threadIdx.x & 31;
+    const int warp = r >> 5;                     // warp within the group
+    constexpr int W = Grp<G>::kWarps;
+    int* cnt = mode == kGlobal ? gtab : slice;
+    const long long zero_n = mode == kLane ? C * G : mode == kWarp ? C * W : C;
+    for (long long k = r; k < zero_n; k += G) cnt[k] = 0;
+    Grp<G>::sync();
     switch (mode) {
-        case kLane: count_dispatch<kLane>(s, cnt + (long long)warp * C * 32 + lane); break;
-        case kWarp: count_dispatch<kWarp>(s, cnt + (long long)warp * C); break;
-        default: count_dispatch<kCta>(s, cnt); break;   // shared or global table
+        case kLane: count_dispatch<G, kLane>(s, cnt + (long long)warp * C * 32 + lane); break;
+        case kWarp: count_dispatch<G, kWarp>(s, cnt + (long long)warp * C); break;
+        default: count_dispatch<G, kShared>(s, cnt); break;
     }
-    __syncthreads();
-
-    // Merge the private copies into one table T.
+    Grp<G>::sync();
     int* T;
-    int* M;   // marginals: Nxz [nz*rx], Nyz [nz*ry], Nzz [nz]
     if (mode == kLane) {
-        T = smem + C * 32 * nw;
-        for (long long c = threadIdx.x; c < C; c += blockDim.x) {
+        T = slice + C * G;
+        for (long long c = r; c < C; c += G) {
             int sum = 0;
-            for (int w = 0; w < nw; ++w) {
+            for (int w = 0; w < W; ++w) {
                 const int* col = cnt + ((long long)w * C + c) * 32;
 #pragma unroll 8
                 for (int l = 0; l < 32; ++l) sum += col[(l + (int)c) & 31];
             }
             T[c] = sum;
         }
-        M = T + C;
+        *M = T + C;
     } else if (mode == kWarp) {
         T = cnt;
-        for (long long c = threadIdx.x; c < C; c += blockDim.x) {
+        for (long long c = r; c < C; c += G) {
             int sum = 0;
-            for (int w = 0; w < nw; ++w) sum += cnt[(long long)w * C + c];
+            for (int w = 0; w < W; ++w) sum += cnt[(long long)w * C + c];
             T[c] = sum;
         }
-        M = smem + C * nw;
-    } else if (mode == kCta) {
+        *M = slice + C * W;
+    } else if (mode == kShared) {
         T = cnt;
-        M = smem + C;
+        *M = slice + C;
     } else {
         T = cnt;
-        M = (marg <= smem_ints) ? smem : gtab + C;
+        *M = marg <= slice_ints ? slice : gtab + C;
     }
-    __syncthreads();
+    Grp<G>::sync();
+    return T;
+}
 
+// Marginals N_x+z [nz*rx], N_+yz [nz*ry], N_++z [nz] into M.
+template <int G>
+__device__ __forceinline__ void grp_marginals(const TestSpec& s, const int* T, int* M)
+{
+    const long long nz = s.cells / (s.rx * s.ry);
     int* Nxz = M;
     int* Nyz = M + nz * s.rx;
     int* Nzz = Nyz + nz * s.ry;
-    for (long long k = threadIdx.x; k < nz * s.rx; k += blockDim.x) {
+    const int r = Grp<G>::rank();
+    for (long long k = r; k < nz * s.rx; k += G) {
         int sum = 0;
         for (int y = 0; y < s.ry; ++y) sum += T[k * s.ry + y];
         Nxz[k] = sum;
     }
-    for (long long k = threadIdx.x; k < nz * s.ry; k += blockDim.x) {
+    for (long long k = r; k < nz * s.ry; k += G) {
         const long long z = k / s.ry;
         const int y = (int)(k - z * s.ry);
         int sum = 0;
         for (int x = 0; x < s.rx; ++x) sum += T[(z * s.rx + x) * s.ry + y];
         Nyz[k] = sum;
     }
-    __syncthreads();
-    for (long long z = threadIdx.x; z < nz; z += blockDim.x) {
+    Grp<G>::sync();
+    for (long long z = r; z < nz; z += G) {
         int sum = 0;
         for (int x = 0; x < s.rx; ++x) sum += Nxz[z * s.rx + x];
         Nzz[z] = sum;
     }
-    __syncthreads();
+    Grp<G>::sync();
+}
 
-    // G^2 = 2 sum N ln(N / E): the ratio N / E = (N_xyz N_++z) / (N_x+z N_+yz)
-    // is formed in exact 64-bit integers and its log taken as log1p of the
-    // exact difference over the denominator.
+// Exact G^2 = 2 sum N ln(N / E) in FP64 (every thread of the group gets it).
+// The ratio N / E = (N_xyz N_++z) / (N_x+z N_+yz) is formed in exact 64-bit
+// integers and its log taken as log1p of the exact difference over the
+// denominator.
+template <int G>
+__device__ __forceinline__ double grp_g2_exact(const TestSpec& s, const int* T, const int* M, double* red,
+                                               int32_t* table_out)
+{
+    const long long nz = s.cells / (s.rx * s.ry);
+    const int rxy = s.rx * s.ry;
+    const int* Nxz = M;
+    const int* Nyz = M + nz * s.rx;
+    const int* Nzz = Nyz + nz * s.ry;
     double acc = 0.0;
-    for (long long c = threadIdx.x; c < C; c += blockDim.x) {
+    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
         const int n = T[c];
         if (table_out) table_out[c] = n;
         if (n == 0) continue;
@@ -322,14 +502,44 @@ __device__ TestResult run_test(const TestSpec& s, int* smem, int smem_ints, int*
         const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
         acc += (double)n * log1p((double)(a - b) / (double)b);
     }
-    const double tot = block_sum(acc, red);
-    TestResult r = {0.0, 0.0, 1.0};
-    if (threadIdx.x == 0) {
-        r.g2 = 2.0 * tot;
-        r.df = (double)(s.rx - 1) * (double)(s.ry - 1) * (double)nz;
-        r.p = chisq_q(r.df, r.g2, status);
+    return 2.0 * grp_sum<G>(acc, red);
+}
+
+// Decision "p > alpha" as "G^2 < crit".  The terms are first evaluated with
+// FP32 logarithms (each within 3.2e-7 of its own magnitude, CUDA's logf and
+// log1pf being within 1 ulp) and summed in FP64, giving G^2 within
+// 1e-6 * sum|term|; only when crit lies inside that band is G^2 recomputed
+// exactly in FP64.
+template <int G>
+__device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, const int* M, double crit,
+                                           double* red)
+{
+    const long long nz = s.cells / (s.rx * s.ry);
+    const int rxy = s.rx * s.ry;
+    const int* Nxz = M;
+    const int* Nyz = M + nz * s.rx;
+    const int* Nzz = Nyz + nz * s.ry;
+    double acc = 0.0, mag = 0.0;
+    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+        const int n = T[c];
+        if (n == 0) continue;
+        const long long z = c / rxy;
+        const int rem = (int)(c - z * rxy);
+        const int x = rem / s.ry, y = rem - x * s.ry;
+        const long long a = (long long)n * Nzz[z];
+        const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
+        const float fb = (float)b;
+        const float delta = (float)(a - b) / fb;
+        const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
+        const float t = (float)n * L;
+        acc += (double)t;
+        mag += (double)fabsf(t);
     }
-    return r;
+    const double g2 = 2.0 * grp_sum<G>(acc, red);
+    const double err = 2.0 * 1e-6 * grp_sum<G>(mag, red) + 1e-9;
+    if (g2 + err < crit) return true;
+    if (g2 - err >= crit) return false;
+    return grp_g2_exact<G>(s, T, M, red, nullptr) < crit;
 }
 
 }  // namespace fbn

@@ -12,13 +12,15 @@ constexpr int kMaxRows = kMaxD + 2;       // S rows + X row + Y row
 constexpr int kBinomCols = kMaxD + 2;     // binomial table columns k = 0..kMaxD+1
 constexpr long long kBinomSat = 1LL << 62;
 constexpr long long kMaxCells = 1LL << 24;  // largest contingency table (cells)
+constexpr int kMaxVars = 32767;           // neighbour positions are stored in 16 bits
 constexpr int kTestThreads = 256;         // threads of a test CTA
-constexpr int kTestWarps = kTestThreads / 32;
+constexpr int kBaseSmem = 512;            // pass bases cached in shared memory
 
-// device status bits, OR-ed into DepthCounters::status
+// device status bits
 constexpr unsigned kStatusTooBig = 1u;    // table over kMaxCells or scratch too small
 constexpr unsigned kStatusNumeric = 2u;   // p-value iteration hit its cap
 constexpr unsigned kStatusSepPool = 4u;   // separating-set pool overflow
+constexpr unsigned kStatusEdges = 8u;     // edge list overflow
 
 // One learning problem (one data set).  Arrays are device pointers.
 struct ProblemDev {
@@ -39,37 +41,56 @@ struct ProblemDev {
 // One edge i<j of the current depth with its rank space: ranks [0, cnt_i) are
 // the X-side conditioning sets (subsets of a(i)\{j}), ranks [cnt_i, total) the
 // Y-side ones (subsets of a(j)\{i}), each side in lexicographic order.
+// posj = index of j in a(i), posi = index of i in a(j).
 struct EdgeWork {
-    int32_t prob, i, j, pad;
+    int32_t prob, i, j;
+    int16_t posj, posi;
     int64_t cnt_i, total;
 };
 
+// Edge classes: tables that fit a warp's share of shared memory run on warp
+// workers, the others on CTA workers.
+constexpr int kClassWarp = 0;
+constexpr int kClassCta = 1;
+
 struct DepthCounters {
-    unsigned long long n_edges;       // edges appended by the edge-list kernel
-    unsigned long long maxc;          // largest chunk count of an edge
-    unsigned long long next_item;     // work-pool claim counter
-    unsigned long long total_items;   // work items of the depth
-    unsigned long long tests;         // CI tests executed
-    unsigned long long tests_oracle;  // tests of the sequential order (gs = 1)
-    unsigned long long removed;       // edges removed
-    unsigned long long sep_used;      // separating-set pool entries in use
-    unsigned long long max_cells;     // upper bound of table cells this depth
-    unsigned long long pad[6];
+    unsigned long long n_edges[2];      // edges per class
+    unsigned long long maxc[2];         // largest chunk count per class
+    unsigned long long next_item[2];    // work-pool claim counters
+    unsigned long long total_items[2];  // work items per class
+    unsigned long long tests;           // CI tests executed
+    unsigned long long tests_oracle;    // tests of the sequential order (gs = 1)
+    unsigned long long removed;         // edges removed
+    unsigned long long sep_used;        // separating-set pool entries in use
+    unsigned long long max_cells[2];    // upper bound of table cells per class
     unsigned int status;
-    unsigned int pad2[3];
+    unsigned int pad[3];
 };
 
-// Work pool of one depth.
+// Cache of critical values, see fbn_device.cuh.
+struct CritTableDev {
+    long long* keys;
+    double* vals;
+    int cap;
+    int pad;
+};
+
+// Work pool of one depth and one edge class.
 struct PoolArgs {
     const ProblemDev* probs;
-    const EdgeWork* edges;
-    unsigned long long* min_accept;   // [E], lowest accepting rank, init = total
-    const int32_t* sorted;            // edges by chunk count, descending
+    const EdgeWork* edges;            // class sub-array
+    unsigned long long* min_accept;   // class sub-array, lowest accepting rank, init = total
+    const int32_t* sorted;            // class edges by chunk count, descending
     const unsigned long long* base;   // [maxc + 1] first item of pass k
-    DepthCounters* ctr;
+    unsigned long long* next_item;
+    const unsigned long long* total_items;
+    unsigned long long* tests;
+    unsigned* status;
     const long long* binom;           // [binom_rows][kBinomCols]
-    int* gscratch;                    // global tables, gscratch_ints per worker
+    int* gscratch;                    // global tables, gscratch_ints per group
     long long gscratch_ints;
+    CritTableDev crit;
+    long long maxc;
     int32_t d;
     int32_t gs;
     int32_t smem_ints;

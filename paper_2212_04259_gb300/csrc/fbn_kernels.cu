@@ -3,16 +3,18 @@
 //
 // Depth pipeline (every kernel runs over all problems of a batch at once):
 //   k_snapshot   a(v) for every vertex: adjacency row -> ascending neighbour list
-//   k_edges      edges i<j with at least one test: rank space |X-side| + |Y-side|
+//   k_edges      edges i<j with at least one test, with their rank space
+//                |X-side| + |Y-side|, split into a warp class (tables that fit
+//                a warp's share of shared memory) and a CTA class
 //   k_chunk_hist / k_scan / k_place
-//                order the edges by chunk count so that pass k of the work pool
-//                is a prefix of that order
-//   k_pool       persistent CI-level work pool (Section IV-B): each CTA claims
-//                work items (one chunk of gs consecutive conditioning sets of one
-//                edge) from a single atomic counter; items are laid out pass by
-//                pass, so every live edge gets its k-th chunk before any edge
-//                gets its (k+1)-th; chunks above an edge's lowest accepting
-//                rank are skipped
+//                order each class by chunk count, so that pass k of the work
+//                pool is a prefix of that order
+//   k_pool<G>    persistent CI-level work pool (Section IV-B): each group (a
+//                warp or a CTA) claims work items -- one chunk of gs
+//                consecutive conditioning sets of one edge -- from one atomic
+//                counter; items are laid out pass by pass, so every live edge
+//                gets its k-th chunk before any edge gets its (k+1)-th; chunks
+//                above an edge's lowest accepting rank are skipped
 //   k_plain      edge-level form (Section IV-A): one CTA per edge, sequential
 //                conditioning sets with early exit
 //   k_apply      end-of-depth removal over the snapshot; the separating set is
@@ -58,9 +60,9 @@ __device__ __forceinline__ long long binom_sat(const long long* B, int brows, in
 
 __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
                         const int32_t* __restrict__ vtx_first, int total_vertices, int d, int gs,
-                        const long long* __restrict__ binom, int brows, EdgeWork* __restrict__ edges,
-                        unsigned long long* __restrict__ min_accept, long long edge_cap,
-                        DepthCounters* ctr)
+                        const long long* __restrict__ binom, int brows, long long warp_cells_cap,
+                        EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
+                        long long edge_cap, DepthCounters* ctr)
 {
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -70,7 +72,7 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
     const int i = g - vtx_first[p];
     const int deg_i = P.deg[i];
     const int32_t* nb = P.nbr + (long long)i * P.n;
-    unsigned long long local_maxc = 0, local_cells = 0;
+    unsigned long long mc[2] = {0, 0}, mcell[2] = {0, 0};
     for (int t0 = 0; t0 < deg_i; t0 += 32) {
         const int t = t0 + lane;
         int j = -1;
@@ -83,43 +85,62 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
                     total = 1;
                 } else {
                     cnt_i = binom_sat(binom, brows, deg_i - 1, d);
-                    const long long cnt_j = binom_sat(binom, brows, P.deg[j] - 1, d);
-                    total = cnt_i + cnt_j;
+                    total = cnt_i + binom_sat(binom, brows, P.deg[j] - 1, d);
                 }
             }
         }
-        const bool take = total > 0;
-        const unsigned m = __ballot_sync(0xffffffffu, take);
-        unsigned long long base = 0;
-        if (lane == 0 && m) base = atomicAdd(&ctr->n_edges, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (take) {
-            const long long e = (long long)base + __popc(m & ((1u << lane) - 1u));
-            if (e < edge_cap) {
-                EdgeWork w;
-                w.prob = p; w.i = i; w.j = j; w.pad = 0;
-                w.cnt_i = cnt_i; w.total = total;
-                edges[e] = w;
-                min_accept[e] = (unsigned long long)total;
+        unsigned long long cells = 0;
+        if (total > 0) {
+            // cells bound r_i r_j max_arity^d
+            cells = (unsigned long long)P.ar[i] * P.ar[j];
+            for (int k = 0; k < d && cells <= (unsigned long long)kMaxCells; ++k)
+                cells *= (unsigned long long)P.max_arity;
+        }
+        const int cls = cells <= (unsigned long long)warp_cells_cap ? kClassWarp : kClassCta;
+        for (int c = 0; c < 2; ++c) {
+            const bool take = total > 0 && cls == c;
+            const unsigned m = __ballot_sync(0xffffffffu, take);
+            unsigned long long base = 0;
+            if (lane == 0 && m) base = atomicAdd(&ctr->n_edges[c], (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (!take) continue;
+            const long long k = (long long)base + __popc(m & ((1u << lane) - 1u));
+            if (k >= edge_cap) {
+                atomicOr(&ctr->status, kStatusEdges);
+                continue;
             }
+            const long long e = c == kClassWarp ? k : edge_cap - 1 - k;
+            // position of i in a(j)
+            const int32_t* nj = P.nbr + (long long)j * P.n;
+            int lo = 0, hi = P.deg[j];
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (nj[mid] < i) lo = mid + 1; else hi = mid;
+            }
+            EdgeWork w;
+            w.prob = p; w.i = i; w.j = j;
+            w.posj = (int16_t)t; w.posi = (int16_t)lo;
+            w.cnt_i = cnt_i; w.total = total;
+            edges[e] = w;
+            min_accept[e] = (unsigned long long)total;
             const unsigned long long ch = (unsigned long long)((total + gs - 1) / gs);
-            local_maxc = ch > local_maxc ? ch : local_maxc;
-            // cells bound: r_i r_j max_arity^d
-            unsigned long long cells = (unsigned long long)P.ar[i] * P.ar[j];
-            for (int k = 0; k < d && cells <= (unsigned long long)kMaxCells; ++k) cells *= (unsigned long long)P.max_arity;
-            local_cells = cells > local_cells ? cells : local_cells;
+            mc[c] = ch > mc[c] ? ch : mc[c];
+            mcell[c] = cells > mcell[c] ? cells : mcell[c];
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long a = __shfl_down_sync(0xffffffffu, local_maxc, o);
-        const unsigned long long b = __shfl_down_sync(0xffffffffu, local_cells, o);
-        local_maxc = a > local_maxc ? a : local_maxc;
-        local_cells = b > local_cells ? b : local_cells;
-    }
-    if (lane == 0) {
-        if (local_maxc) atomicMax(&ctr->maxc, local_maxc);
-        if (local_cells) atomicMax(&ctr->max_cells, local_cells);
+    for (int c = 0; c < 2; ++c) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long a = __shfl_down_sync(0xffffffffu, mc[c], o);
+            const unsigned long long b = __shfl_down_sync(0xffffffffu, mcell[c], o);
+            mc[c] = a > mc[c] ? a : mc[c];
+            mcell[c] = b > mcell[c] ? b : mcell[c];
+        }
+        if (lane == 0) {
+            if (mc[c]) atomicMax(&ctr->maxc[c], mc[c]);
+            if (mcell[c]) atomicMax(&ctr->max_cells[c], mcell[c]);
+        }
     }
 }
 
@@ -135,58 +156,68 @@ __global__ void k_chunk_hist(const EdgeWork* __restrict__ edges, long long E, in
 
 // One CTA: alive[k] = #edges with more than k chunks (k = 0..maxc), base[k] =
 // sum_{k' < k} alive[k'] (k = 0..maxc).  base[maxc] is the item count.
+// Block-wide scans over contiguous per-thread segments.
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        unsigned long long s = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    const unsigned long long before = warp > 0 ? sh[warp - 1] : 0;
+    __syncthreads();
+    return before + x - v;
+}
+
 __global__ void k_scan(const unsigned long long* __restrict__ hist, long long maxc,
                        unsigned long long* __restrict__ alive, unsigned long long* __restrict__ base,
-                       DepthCounters* ctr)
+                       unsigned long long* total_items, unsigned long long* next_item)
 {
-    __shared__ unsigned long long part[1024];
+    __shared__ unsigned long long sh[32];
     const int T = blockDim.x;
     const long long len = maxc + 1;
     const long long seg = (len + T - 1) / T;
-    // suffix sums of hist: alive[k] = sum_{c > k} hist[c]
-    const long long lo = (long long)threadIdx.x * seg, hi = lo + seg < len ? lo + seg : len;
+    // alive[c] = sum_{c' > c} hist[c']: thread t owns the t-th segment counted
+    // from the end of the array, so an exclusive scan in thread order sums the
+    // segments that lie after this thread's one
+    long long lo = len - (long long)(threadIdx.x + 1) * seg, hi = len - (long long)threadIdx.x * seg;
+    if (lo < 0) lo = 0;
+    if (hi < 0) hi = 0;
     unsigned long long s = 0;
     for (long long c = lo; c < hi; ++c) s += hist[c];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {  // exclusive suffix scan of the segment sums
-        unsigned long long run = 0;
-        for (int t = T - 1; t >= 0; --t) {
-            const unsigned long long v = part[t];
-            part[t] = run;
-            run += v;
-        }
-    }
-    __syncthreads();
-    unsigned long long run = part[threadIdx.x];   // sum of hist over later segments
+    unsigned long long run = block_exclusive_scan(s, sh);
     for (long long c = hi - 1; c >= lo; --c) {
-        alive[c] = run;                           // sum over c' > c
+        alive[c] = run;
         run += hist[c];
     }
     __syncthreads();
-    // prefix sums of alive: base[k] = sum_{k' < k} alive[k']
+    // base[k] = sum_{k' < k} alive[k'], segments in forward order
+    const long long flo = (long long)threadIdx.x * seg, fhi = flo + seg < len ? flo + seg : len;
     s = 0;
-    for (long long c = lo; c < hi; ++c) s += alive[c];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long r = 0;
-        for (int t = 0; t < T; ++t) {
-            const unsigned long long v = part[t];
-            part[t] = r;
-            r += v;
-        }
-    }
-    __syncthreads();
-    run = part[threadIdx.x];
-    for (long long c = lo; c < hi; ++c) {
+    for (long long c = flo; c < fhi; ++c) s += alive[c];
+    run = block_exclusive_scan(s, sh);
+    for (long long c = flo; c < fhi; ++c) {
         base[c] = run;
         run += alive[c];
     }
-    if (hi == len && lo < hi) {
-        // base[maxc] already written above as the sum over k < maxc; alive[maxc] == 0
-        ctr->total_items = base[maxc];
-        ctr->next_item = 0;
+    if (fhi == len && flo < fhi) {
+        *total_items = base[maxc];
+        *next_item = 0;
     }
 }
 
@@ -202,141 +233,159 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long E, int gs,
 }
 
 // --------------------------------------------------------------------------
-// Fill the test of rank r of edge w into the shared TestSpec (leader only).
-// pos holds the subset positions; when `fresh` the positions are unranked,
-// otherwise they are advanced from the previous rank of the same side.
-__device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& w, int d, long long r,
-                                           bool fresh, int* pos, const long long* binom,
-                                           TestSpec& s, unsigned* status)
+// Per-group state of a worker, in shared memory.
+struct GroupState {
+    long long r0, r1;
+    int e;
+    int go;
+    double crit;
+    int pos[kMaxD];
+};
+
+// Fill the test of rank rk of edge w into the group's TestSpec.  Rank 0 of
+// the group computes the subset positions (unranked when `fresh`, else the
+// successor of the previous rank of the same side); one thread per
+// conditioning variable then resolves its row.  Returns false (uniformly)
+// when the table is over the cell limit.
+template <int G>
+__device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& w, int d, long long rk, bool fresh,
+                                           GroupState& S, const long long* binom, TestSpec& spec, unsigned* status)
 {
-    const bool xside = r < w.cnt_i;
+    const int r = Grp<G>::rank();
+    const bool xside = rk < w.cnt_i;
     const int a = xside ? w.i : w.j;
-    const int b = xside ? w.j : w.i;
-    const long long lr = xside ? r : r - w.cnt_i;
-    const int deg_a = P.deg[a];
-    const int32_t* nb = P.nbr + (long long)a * P.n;
-    if (d > 0) {
-        const int p = deg_a - 1;
-        if (fresh || lr == 0) unrank_lex(lr, p, d, binom, pos);
-        else next_subset(p, d, pos);
-        // position of b in a's ascending list
-        int lo = 0, hi = deg_a;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (nb[mid] < b) lo = mid + 1; else hi = mid;
+    const int posb = xside ? w.posj : w.posi;
+    if (r == 0) {
+        if (d > 0) {
+            const long long lr = xside ? rk : rk - w.cnt_i;
+            const int p = P.deg[a] - 1;
+            if (fresh || lr == 0) unrank_lex(lr, p, d, binom, S.pos);
+            else next_subset(p, d, S.pos);
         }
-        const int posb = lo;
-        for (int k = 0; k < d; ++k) {
-            const int t = pos[k];
-            const int v = nb[t < posb ? t : t + 1];
-            s.rows[k] = P.data + (long long)v * P.ld;
-            s.rad[k] = P.ar[v];
-        }
+        spec.nrows = d + 2;
+        spec.N = P.N;
     }
-    s.rows[d] = P.data + (long long)w.i * P.ld;
-    s.rad[d] = P.ar[w.i];
-    s.rows[d + 1] = P.data + (long long)w.j * P.ld;
-    s.rad[d + 1] = P.ar[w.j];
-    s.nrows = d + 2;
-    s.rx = P.ar[w.i];
-    s.ry = P.ar[w.j];
-    s.N = P.N;
+    Grp<G>::sync();
+    if (r < d) {
+        const int t = S.pos[r];
+        const int v = P.nbr[(long long)a * P.n + (t < posb ? t : t + 1)];
+        spec.rows[r] = P.data + (long long)v * P.ld;
+        spec.rad[r] = P.ar[v];
+    } else if (r == d) {
+        spec.rows[d] = P.data + (long long)w.i * P.ld;
+        spec.rad[d] = spec.rx = P.ar[w.i];
+    } else if (r == d + 1) {
+        spec.rows[d + 1] = P.data + (long long)w.j * P.ld;
+        spec.rad[d + 1] = spec.ry = P.ar[w.j];
+    }
+    Grp<G>::sync();
     long long cells = 1;
-    for (int k = 0; k < d + 2; ++k) {
-        cells *= s.rad[k];
-        if (cells > kMaxCells) break;
-    }
-    s.cells = cells;
+    for (int k = 0; k < d + 2 && cells <= kMaxCells; ++k) cells *= spec.rad[k];
     if (cells > kMaxCells) {
-        atomicOr(status, kStatusTooBig);
+        if (r == 0) atomicOr(status, kStatusTooBig);
         return false;
     }
+    if (r == 0) spec.cells = cells;
+    Grp<G>::sync();
     return true;
 }
 
-__global__ void __launch_bounds__(kTestThreads) k_pool(PoolArgs a, unsigned long long maxc)
+// Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
+template <int G>
+__device__ __forceinline__ int run_rank(const PoolArgs& a, const ProblemDev& P, const EdgeWork& w, long long rk,
+                                        bool fresh, GroupState& S, TestSpec& spec, int* slice, long long slice_ints,
+                                        int* gtab, double* red)
+{
+    if (!setup_rank<G>(P, w, a.d, rk, fresh, S, a.binom, spec, a.status)) return -1;
+    int* M = nullptr;
+    const int* T = grp_table<G>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
+    if (!T) {
+        if (Grp<G>::rank() == 0) atomicOr(a.status, kStatusTooBig);
+        return -1;
+    }
+    grp_marginals<G>(spec, T, M);
+    if (Grp<G>::rank() == 0) {
+        const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
+        S.crit = crit_get(a.crit, df, a.alpha, a.status);
+        atomicAdd(a.tests, 1ULL);
+    }
+    Grp<G>::sync();
+    return grp_decide<G>(spec, T, M, S.crit, red) ? 1 : 0;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kTestThreads, G == kTestThreads ? 2 : 3) k_pool(PoolArgs a)
 {
     extern __shared__ int smem[];
-    __shared__ TestSpec spec;
+    constexpr int NG = kTestThreads / G;   // groups per CTA
+    __shared__ TestSpec spec_s[NG];
+    __shared__ GroupState st_s[NG];
     __shared__ double red[32];
-    __shared__ unsigned long long s_item;
-    __shared__ int s_edge;
-    __shared__ long long s_r0, s_r1;
-    __shared__ int s_go;
-    __shared__ int s_pos[kMaxD];
-    int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
-    const unsigned long long total_items = a.ctr->total_items;
-    unsigned* status = &a.ctr->status;
+    __shared__ unsigned long long base_s[kBaseSmem];
+    const int g = Grp<G>::gid();
+    const int r = Grp<G>::rank();
+    const long long slice_ints = a.smem_ints / NG;
+    int* slice = smem + g * slice_ints;
+    int* gtab = a.gscratch ? a.gscratch + ((long long)blockIdx.x * NG + g) * a.gscratch_ints : nullptr;
+    const unsigned long long total = *a.total_items;
+    const bool base_in_smem = a.maxc + 1 <= kBaseSmem;
+    if (base_in_smem)
+        for (long long k = threadIdx.x; k <= a.maxc; k += blockDim.x) base_s[k] = a.base[k];
+    __syncthreads();
+    const unsigned long long* base = base_in_smem ? base_s : a.base;
+    GroupState& S = st_s[g];
+    TestSpec& spec = spec_s[g];
 
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long w = atomicAdd(&a.ctr->next_item, 1ULL);
-            s_item = w;
-            if (w < total_items) {
-                // pass k = largest k with base[k] <= w
-                long long lo = 0, hi = (long long)maxc - 1;
+        if (r == 0) {
+            const unsigned long long w = atomicAdd(a.next_item, 1ULL);
+            S.e = -1;
+            if (w < total) {
+                long long lo = 0, hi = a.maxc - 1;   // pass k: largest k with base[k] <= w
                 while (lo < hi) {
                     const long long mid = (lo + hi + 1) >> 1;
-                    if (a.base[mid] <= w) lo = mid; else hi = mid - 1;
+                    if (base[mid] <= w) lo = mid; else hi = mid - 1;
                 }
-                const int e = a.sorted[w - a.base[lo]];
+                const int e = a.sorted[w - base[lo]];
                 const long long r0 = lo * (long long)a.gs;
                 const long long tot = a.edges[e].total;
-                s_edge = e;
-                s_r0 = r0;
-                s_r1 = r0 + a.gs < tot ? r0 + a.gs : tot;
+                S.e = e;
+                S.r0 = r0;
+                S.r1 = r0 + a.gs < tot ? r0 + a.gs : tot;
             }
         }
-        __syncthreads();
-        if (s_item >= total_items) break;
-        const int e = s_edge;
+        Grp<G>::sync();
+        const int e = S.e;
+        if (e < 0) break;
         const EdgeWork w = a.edges[e];
         const ProblemDev& P = a.probs[w.prob];
-        for (long long r = s_r0; r < s_r1; ++r) {
-            if (threadIdx.x == 0) {
-                const unsigned long long ma = *((volatile unsigned long long*)&a.min_accept[e]);
-                s_go = ((unsigned long long)r <= ma) &&
-                       setup_rank(P, w, a.d, r, r == s_r0, s_pos, a.binom, spec, status);
-            }
-            __syncthreads();
-            if (!s_go) break;
-            const TestResult res = run_test(spec, smem, a.smem_ints, gtab, a.gscratch_ints, nullptr, status, red);
-            if (threadIdx.x == 0) {
-                atomicAdd(&a.ctr->tests, 1ULL);
-                s_go = !(res.p > a.alpha);
-                if (!s_go) atomicMin(&a.min_accept[e], (unsigned long long)r);
-            }
-            __syncthreads();
-            if (!s_go) break;
+        const long long r0 = S.r0, r1 = S.r1;
+        for (long long rk = r0; rk < r1; ++rk) {
+            if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&a.min_accept[e]);
+            Grp<G>::sync();
+            if (!S.go) break;
+            const int res = run_rank<G>(a, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, red);
+            if (res == 1 && r == 0) atomicMin(&a.min_accept[e], (unsigned long long)rk);
+            if (res != 0) break;
         }
-        __syncthreads();
+        Grp<G>::sync();
     }
 }
 
-__global__ void __launch_bounds__(kTestThreads) k_plain(PoolArgs a, long long E)
+__global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a, long long E)
 {
     extern __shared__ int smem[];
     __shared__ TestSpec spec;
+    __shared__ GroupState S;
     __shared__ double red[32];
-    __shared__ int s_go;
-    __shared__ int s_pos[kMaxD];
     int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
-    unsigned* status = &a.ctr->status;
     for (long long e = blockIdx.x; e < E; e += gridDim.x) {
         const EdgeWork w = a.edges[e];
         const ProblemDev& P = a.probs[w.prob];
-        for (long long r = 0; r < w.total; ++r) {
-            if (threadIdx.x == 0) s_go = setup_rank(P, w, a.d, r, r == 0, s_pos, a.binom, spec, status);
-            __syncthreads();
-            if (!s_go) break;
-            const TestResult res = run_test(spec, smem, a.smem_ints, gtab, a.gscratch_ints, nullptr, status, red);
-            if (threadIdx.x == 0) {
-                atomicAdd(&a.ctr->tests, 1ULL);
-                s_go = !(res.p > a.alpha);
-                if (!s_go) a.min_accept[e] = (unsigned long long)r;
-            }
-            __syncthreads();
-            if (!s_go) break;
+        for (long long rk = 0; rk < w.total; ++rk) {
+            const int res = run_rank<kTestThreads>(a, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
+            if (res == 1 && threadIdx.x == 0) a.min_accept[e] = (unsigned long long)rk;
+            if (res != 0) break;
         }
         __syncthreads();
     }
@@ -367,14 +416,12 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
             atomicOr(&ctr->status, kStatusSepPool);
         } else {
             const bool xside = (long long)ma < w.cnt_i;
-            const int a = xside ? w.i : w.j, b = xside ? w.j : w.i;
+            const int a = xside ? w.i : w.j;
+            const int posb = xside ? w.posj : w.posi;
             const long long lr = xside ? (long long)ma : (long long)ma - w.cnt_i;
             int pos[kMaxD];
-            const int deg_a = P.deg[a];
-            unrank_lex(lr, deg_a - 1, d, binom, pos);
+            unrank_lex(lr, P.deg[a] - 1, d, binom, pos);
             const int32_t* nb = P.nbr + (long long)a * n;
-            int posb = 0;
-            while (posb < deg_a && nb[posb] < b) ++posb;
             for (int k = 0; k < d; ++k) sep_pool[off + k] = nb[pos[k] < posb ? pos[k] : pos[k] + 1];
         }
     }
@@ -383,6 +430,7 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
 }
 
 // --------------------------------------------------------------------------
+// Explicit tests (fbn_ci_test / fbn_ci_table): exact FP64 G^2 and p-value.
 __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __restrict__ prob,
                                                            const CiTestDesc* __restrict__ tests, int ntests,
                                                            double* __restrict__ out, int32_t* table_out,
@@ -412,10 +460,7 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
         spec.rx = P.ar[q.x];
         spec.ry = P.ar[q.y];
         spec.N = P.N;
-        for (int k = 0; k < d + 2; ++k) {
-            cells *= spec.rad[k];
-            if (cells > kMaxCells) break;
-        }
+        for (int k = 0; k < d + 2 && cells <= kMaxCells; ++k) cells *= spec.rad[k];
         spec.cells = cells;
         s_ok = cells <= kMaxCells;
         if (!s_ok) atomicOr(status, kStatusTooBig);
@@ -423,11 +468,19 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
     __syncthreads();
     if (!s_ok) return;
     int* gtab = gscratch ? gscratch + (long long)t * gscratch_ints : nullptr;
-    const TestResult r = run_test(spec, smem, smem_ints, gtab, gscratch_ints, table_out, status, red);
+    int* M = nullptr;
+    const int* T = grp_table<kTestThreads>(spec, smem, smem_ints, gtab, gscratch_ints, &M);
+    if (!T) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusTooBig);
+        return;
+    }
+    grp_marginals<kTestThreads>(spec, T, M);
+    const double g2 = grp_g2_exact<kTestThreads>(spec, T, M, red, table_out);
     if (threadIdx.x == 0) {
-        out[3 * t + 0] = r.g2;
-        out[3 * t + 1] = r.df;
-        out[3 * t + 2] = r.p;
+        const double df = (double)(spec.rx - 1) * (double)(spec.ry - 1) * (double)(spec.cells / (spec.rx * spec.ry));
+        out[3 * t + 0] = g2;
+        out[3 * t + 1] = df;
+        out[3 * t + 2] = chisq_q(df, g2, status);
     }
 }
 
@@ -442,30 +495,38 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
 }
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                  int total_vertices, int d, int gs, const long long* binom, int brows, EdgeWork* edges,
-                  unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr, cudaStream_t st)
+                  int total_vertices, int d, int gs, const long long* binom, int brows, long long warp_cells_cap,
+                  EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
+                  cudaStream_t st)
 {
     const int warps = 8;
     k_edges<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(
-        probs, vtx_prob, vtx_first, total_vertices, d, gs, binom, brows, edges, min_accept, edge_cap, ctr);
+        probs, vtx_prob, vtx_first, total_vertices, d, gs, binom, brows, warp_cells_cap, edges, min_accept,
+        edge_cap, ctr);
 }
 
 void launch_order(const EdgeWork* edges, long long E, int gs, long long maxc, unsigned long long* hist,
                   unsigned long long* alive, unsigned long long* base, unsigned long long* cursor,
-                  int32_t* sorted, DepthCounters* ctr, cudaStream_t st)
+                  int32_t* sorted, unsigned long long* total_items, unsigned long long* next_item,
+                  cudaStream_t st)
 {
     cudaMemsetAsync(hist, 0, (maxc + 1) * sizeof(unsigned long long), st);
     cudaMemsetAsync(cursor, 0, (maxc + 1) * sizeof(unsigned long long), st);
     const int T = 256;
     const unsigned blocks = (unsigned)((E + T - 1) / T);
     k_chunk_hist<<<blocks, T, 0, st>>>(edges, E, gs, hist);
-    k_scan<<<1, 1024, 0, st>>>(hist, maxc, alive, base, ctr);
+    k_scan<<<1, 1024, 0, st>>>(hist, maxc, alive, base, total_items, next_item);
     k_place<<<blocks, T, 0, st>>>(edges, E, gs, alive, cursor, sorted);
 }
 
-void launch_pool(const PoolArgs& a, unsigned long long maxc, int grid, size_t smem_bytes, cudaStream_t st)
+void launch_pool(const PoolArgs& a, int group, int grid, size_t smem_bytes, cudaStream_t st)
 {
-    k_pool<<<grid, kTestThreads, smem_bytes, st>>>(a, maxc);
+    switch (group) {
+        case 32: k_pool<32><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
+        case 64: k_pool<64><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
+        case 128: k_pool<128><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
+        default: k_pool<kTestThreads><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
+    }
 }
 
 void launch_plain(const PoolArgs& a, long long E, int grid, size_t smem_bytes, cudaStream_t st)
@@ -490,18 +551,29 @@ void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests
                                                          gscratch_ints, status, (int)(smem_bytes / 4));
 }
 
-cudaError_t set_kernel_smem(size_t smem_bytes)
+cudaError_t set_kernel_smem(size_t max_smem)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_pool, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes))) return e;
-    if ((e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes))) return e;
-    return cudaFuncSetAttribute(k_ci_tests, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    const int b = (int)max_smem;
+    if ((e = cudaFuncSetAttribute(k_pool<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool<kTestThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    return cudaFuncSetAttribute(k_ci_tests, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
-int pool_blocks_per_sm(size_t smem_bytes)
+int pool_blocks_per_sm(int group, size_t smem_bytes)
 {
     int nb = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool, kTestThreads, smem_bytes);
+    switch (group) {
+        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<32>, kTestThreads, smem_bytes); break;
+        case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<64>, kTestThreads, smem_bytes); break;
+        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<128>, kTestThreads, smem_bytes); break;
+        default:
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<kTestThreads>, kTestThreads, smem_bytes);
+            break;
+    }
     return nb;
 }
 
