@@ -154,6 +154,36 @@ const char* fbn_last_error(const fbn_handle* h);
 /* fbn_destroy -- free the handle and its device memory (NULL is a no-op). */
 void fbn_destroy(fbn_handle* h);
 
+/* fbn_ci_test_noalloc -- the test of fbn_ci_test for callers that cannot
+ * allocate device memory: a process whose device memory belongs to another
+ * allocator (a framework's caching allocator, or a server that reserves a
+ * fixed budget at start-up) or a latency-critical loop where cudaMalloc and
+ * cudaFree would stall the device.  The paper has no counterpart: this is an
+ * interface for such callers, not a step of the method.
+ *   data     : device, uint8 [n_vars][ld] variable-major, 16-byte aligned,
+ *              ld >= n_samples and a multiple of 16; values must lie below
+ *              their arity (not checked here).
+ *   arities  : host, uint8 [n_vars], each >= 2.
+ *   x, y, z, nz : as in fbn_ci_test (z in host memory).
+ *   out      : device, 3 doubles written in stream order: G^2, df, p
+ *              (p = NaN if the p-value iteration failed).
+ *   table_out: device, nullable; int32 counts in the fbn_ci_table layout.
+ *   stream   : cudaStream_t (NULL = the legacy default stream).
+ * The call is asynchronous and allocates nothing: it calls no cudaMalloc,
+ * cudaFree or allocating library routine.  Its scratch is one fixed 3 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits; tables above 2^18 = 262,144 cells are
+ * rejected with FBN_ETOOBIG.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) and sets the kernel's
+ * shared-memory limit, so make that first call before any stream capture.
+ * All calls on a device share the one scratch array: calls that overlap on
+ * the GPU (different streams, or other host threads) race and must be
+ * serialised by the caller.  Errors: FBN_EINVAL, FBN_ETOOBIG, FBN_ECUDA, with
+ * the reason in fbn_last_error(NULL). */
+int fbn_ci_test_noalloc(const uint8_t* data, int64_t ld, int32_t n_vars, int64_t n_samples,
+                        const uint8_t* arities, int32_t x, int32_t y, const int32_t* z, int32_t nz,
+                        double* out, int32_t* table_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

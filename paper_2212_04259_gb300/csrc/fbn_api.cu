@@ -589,6 +589,11 @@ void free_handle(fbn_handle* h)
 
 }  // namespace
 
+void fbn::fbn_internal_set_error(const char* msg)
+{
+    g_create_error = msg;
+}
+
 // ==========================================================================
 extern "C" {
 

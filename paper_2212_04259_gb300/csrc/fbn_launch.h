@@ -34,6 +34,8 @@ void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
                      size_t smem_bytes, cudaStream_t st);
 cudaError_t set_kernel_smem(size_t max_smem);
+// Sets the message fbn_last_error(NULL) returns.
+void fbn_internal_set_error(const char* msg);
 int pool_blocks_per_sm(int group, size_t smem_bytes);
 
 }  // namespace fbn

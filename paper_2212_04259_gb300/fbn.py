@@ -25,7 +25,7 @@ MAX_DEPTHS = 64
 # Every symbol include/fbn.h declares.
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_get_stats",
-           "fbn_last_error", "fbn_destroy")
+           "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc")
 
 
 class FbnError(RuntimeError):
@@ -83,6 +83,8 @@ def lib():
         L.fbn_last_error.argtypes = [p]
         L.fbn_destroy.restype = None
         L.fbn_destroy.argtypes = [p]
+        L.fbn_ci_test_noalloc.restype = C.c_int
+        L.fbn_ci_test_noalloc.argtypes = [p, i64, i32, i64, p, i32, i32, p, i32, p, p, p]
         _lib = L
         return L
 
@@ -245,3 +247,20 @@ def fbn_destroy(h: Handle) -> None:
     if h.ptr:
         lib().fbn_destroy(h.ptr)
         h.ptr = None
+
+
+def fbn_ci_test_noalloc(data_dev, ld: int, n_samples: int, arities, x: int, y: int, z, out_dev,
+                        table_dev=None, stream=None) -> None:
+    """Enqueue one CI test on caller-owned device buffers, allocating nothing.
+
+    data_dev: device uint8 tensor holding [n_vars][ld] rows; out_dev: device
+    float64 tensor of 3 (G^2, df, p), written in stream order; table_dev:
+    optional device int32 tensor for the counts.  stream: torch.cuda.Stream,
+    raw handle or None (the legacy default stream)."""
+    ar = np.ascontiguousarray(arities, dtype=np.uint8)
+    za = _zarr(z)
+    raw = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+    rc = lib().fbn_ci_test_noalloc(_ptr(data_dev), int(ld), len(ar), int(n_samples), _ptr(ar), x, y,
+                                   _ptr(za) if len(za) else None, len(za), _ptr(out_dev),
+                                   _ptr(table_dev), C.c_void_p(raw) if raw else None)
+    _check(rc)
