@@ -236,7 +236,7 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
         oracle_result_free(r);
         return NULL;
     }
-    /* Line 1: complete undirected graph. */
+    /* Algorithm 1 starts from the complete undirected graph. */
     for (int32_t i = 0; i < n; i++)
         for (int32_t j = 0; j < n; j++) {
             r->adj[(int64_t)i * n + j] = (uint8_t)(i != j);
@@ -245,13 +245,14 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
 
     for (int32_t d = 0;; d++) {
         if (max_depth >= 0 && d > max_depth) break;
-        /* Lines 4-6: snapshot a(V_i) of every node, ascending. */
+        /* Snapshot a(V_i) of every node, ascending (Algorithm 1). */
         for (int32_t i = 0; i < n; i++) {
             deg[i] = 0;
             for (int32_t j = 0; j < n; j++)
                 if (r->adj[(int64_t)i * n + j]) nbr[(int64_t)i * n + deg[i]++] = j;
         }
-        /* Line 20, evaluated on this depth's snapshot: is any side big enough? */
+        /* Termination test of Algorithm 1, evaluated on this depth's snapshot:
+         * does any edge have a side with at least d candidates? */
         int any = 0;
         for (int32_t i = 0; i < n && !any; i++)
             for (int32_t k = 0; k < deg[i]; k++)
@@ -261,7 +262,7 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
         r->depths = d + 1;
         memset(remove, 0, (size_t)nn);
 
-        /* Lines 7-16: every edge i<j of the snapshot. */
+        /* Every edge i<j of the snapshot (Algorithm 1). */
         for (int32_t i = 0; i < n; i++) {
             for (int32_t kk = 0; kk < deg[i]; kk++) {
                 int32_t j = nbr[(int64_t)i * n + kk];
@@ -286,7 +287,7 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
                         }
                         r->tests[slot]++;
                         if (fabs(pv - alpha) <= near_tol) near_push(r, i, j, d, pv);
-                        if (pv > alpha) {               /* Lines 13-15 */
+                        if (pv > alpha) {               /* independent: remove, keep S */
                             found = 1;
                             remove[(int64_t)i * n + j] = 1;
                             int32_t* s = (int32_t*)malloc((size_t)(d > 0 ? d : 1) * sizeof(int32_t));

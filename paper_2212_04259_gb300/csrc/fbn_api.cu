@@ -369,7 +369,7 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
         if (rc) return rc;
         const long long Ec[2] = {(long long)ws.h_ctr->n_edges[0], (long long)ws.h_ctr->n_edges[1]};
         const long long E = Ec[0] + Ec[1];
-        if (E == 0) break;   // no edge has a side with >= d candidates (Algorithm 1, last line)
+        if (E == 0) break;   // no edge has a side with >= d candidates: Algorithm 1 stops
         const long long maxc[2] = {(long long)ws.h_ctr->maxc[0], (long long)ws.h_ctr->maxc[1]};
         const long long mcells[2] = {(long long)ws.h_ctr->max_cells[0], (long long)ws.h_ctr->max_cells[1]};
         if (mcells[1] > kMaxCells)
