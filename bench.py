@@ -377,6 +377,9 @@ def main():
                 "cpu_baseline": cpu, "plain_form": plain,
                 "tests_per_step": {"oracle_equivalent": tests, "executed": sum(st["tests"]),
                                    "per_depth_oracle": st["tests_oracle"]},
+                "per_depth": {"edges": st["edges"], "tests_executed": st["tests"],
+                              "ms": [round(x, 4) for x in st["ms"]],
+                              "test_kernel_ms": [round(x, 4) for x in st["test_ms"]]},
                 "skeleton_ms": ms, "wall_s": wall}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -214,12 +214,41 @@ __device__ __forceinline__ T grp_sum(T v, T* red)
     return t;
 }
 
+// Two sums in one pass (red: the CTA's scratch of 32 doubles).
+template <int G>
+__device__ __forceinline__ void grp_sum2(double& a, double& b, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (G == 32) return;
+    double* r = red + Grp<G>::gid() * 2 * Grp<G>::kWarps;
+    Grp<G>::sync();
+    if ((threadIdx.x & 31) == 0) {
+        r[2 * (Grp<G>::rank() >> 5)] = a;
+        r[2 * (Grp<G>::rank() >> 5) + 1] = b;
+    }
+    Grp<G>::sync();
+    a = 0.0;
+    b = 0.0;
+#pragma unroll
+    for (int w = 0; w < Grp<G>::kWarps; ++w) {
+        a += r[2 * w];
+        b += r[2 * w + 1];
+    }
+}
+
 enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3 };
 
 template <int MODE>
 __device__ __forceinline__ void bump(int* base, unsigned idx)
 {
-    if (MODE == kLane) base[idx * 32u] += 1;        // this lane's private column: no race, no atomic
+    // kLane: this lane's private column, so no other thread touches the word;
+    // the update is still a shared-memory reduction (red.shared.add) rather
+    // than load-add-store, so consecutive samples do not wait on each other
+    if (MODE == kLane) atomicAdd(base + idx * 32u, 1);
     else atomicAdd(base + idx, 1);
 }
 
@@ -417,14 +446,23 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
     Grp<G>::sync();
     int* T;
     if (mode == kLane) {
+        // stage 1: each warp folds its 32 lane columns, lane l taking cells
+        // c = l, l + 32, ...; the sum goes to column (c mod 32) of cell c's
+        // row, which only that lane touches (and which keeps stage 2 free of
+        // bank conflicts).  stage 2: fold the warps' partial sums.
+        int* own = cnt + (long long)warp * C * 32;
+        for (long long c = lane; c < C; c += 32) {
+            const int* col = own + c * 32;
+            int sum = 0;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) sum += col[(l + (int)c) & 31];
+            own[c * 32 + (c & 31)] = sum;
+        }
+        Grp<G>::sync();
         T = slice + C * G;
         for (long long c = r; c < C; c += G) {
             int sum = 0;
-            for (int w = 0; w < W; ++w) {
-                const int* col = cnt + ((long long)w * C + c) * 32;
-#pragma unroll 8
-                for (int l = 0; l < 32; ++l) sum += col[(l + (int)c) & 31];
-            }
+            for (int w = 0; w < W; ++w) sum += cnt[((long long)w * C + c) * 32 + (c & 31)];
             T[c] = sum;
         }
         *M = T + C;
@@ -506,10 +544,13 @@ __device__ __forceinline__ double grp_g2_exact(const TestSpec& s, const int* T, 
 }
 
 // Decision "p > alpha" as "G^2 < crit".  The terms are first evaluated with
-// FP32 logarithms (each within 3.2e-7 of its own magnitude, CUDA's logf and
-// log1pf being within 1 ulp) and summed in FP64, giving G^2 within
-// 1e-6 * sum|term|; only when crit lies inside that band is G^2 recomputed
-// exactly in FP64.
+// FP32 logarithms -- each within 3.2e-7 of its own magnitude, CUDA's logf and
+// log1pf being within 1 ulp and the ratio formed from exact 64-bit integers --
+// and summed in FP32: a thread adds at most ceil(C/G) terms and the group tree
+// adds log2(G) levels, each addition erring by at most 6e-8 of the running
+// sum of magnitudes.  G^2 is thus within 2 (3.2e-7 + (ceil(C/G) + log2 G) 6e-8)
+// sum|term| of its exact value (doubled below for margin); only when crit lies
+// inside that band is G^2 recomputed exactly in FP64.
 template <int G>
 __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, const int* M, double crit,
                                            double* red)
@@ -519,7 +560,7 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
     const int* Nxz = M;
     const int* Nyz = M + nz * s.rx;
     const int* Nzz = Nyz + nz * s.ry;
-    double acc = 0.0, mag = 0.0;
+    float acc = 0.0f, mag = 0.0f;
     for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
         const int n = T[c];
         if (n == 0) continue;
@@ -532,11 +573,36 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
         const float delta = (float)(a - b) / fb;
         const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
         const float t = (float)n * L;
-        acc += (double)t;
-        mag += (double)fabsf(t);
+        acc += t;
+        mag += fabsf(t);
     }
-    const double g2 = 2.0 * grp_sum<G>(acc, red);
-    const double err = 2.0 * 1e-6 * grp_sum<G>(mag, red) + 1e-9;
+    float2 v = make_float2(acc, mag);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    if (G > 32) {
+        float* r = reinterpret_cast<float*>(red) + Grp<G>::gid() * 2 * Grp<G>::kWarps;
+        Grp<G>::sync();
+        if ((threadIdx.x & 31) == 0) {
+            r[2 * (Grp<G>::rank() >> 5)] = v.x;
+            r[2 * (Grp<G>::rank() >> 5) + 1] = v.y;
+        }
+        Grp<G>::sync();
+        v.x = 0.0f;
+        v.y = 0.0f;
+#pragma unroll
+        for (int w = 0; w < Grp<G>::kWarps; ++w) {
+            v.x += r[2 * w];
+            v.y += r[2 * w + 1];
+        }
+    }
+    const double per_thread = (double)((s.cells + G - 1) / G);
+    const double levels = (G == 32 ? 5.0 : G == 64 ? 6.0 : G == 128 ? 7.0 : 8.0);
+    const double rel = 2.0 * (3.2e-7 + (per_thread + levels) * 6e-8);
+    const double g2 = 2.0 * (double)v.x;
+    const double err = 2.0 * rel * (double)v.y * 1.0001 + 1e-9;
     if (g2 + err < crit) return true;
     if (g2 - err >= crit) return false;
     return grp_g2_exact<G>(s, T, M, red, nullptr) < crit;
