@@ -106,6 +106,16 @@ int fbn_ci_test(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t n
 int fbn_ci_table(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz,
                  int32_t* counts, int64_t cap);
 
+/* fbn_pairwise_counts -- the depth-0 contingency tables of every pair at once
+ * (Section IV-B: depth zero tests each pair of the complete graph), as the
+ * one-hot Gram matrix computed on the tensor cores.  With M = sum_v r_v and
+ * off_v = sum_{u<v} r_u, counts is an int32 [M][M] host or device buffer and
+ * counts[(off_i + x) * M + off_j + y] = #{samples with V_i = x and V_j = y}
+ * (symmetric; the diagonal blocks hold the marginal counts of one variable).
+ * cap is the capacity of counts in elements (>= M*M).  Errors: FBN_EINVAL,
+ * FBN_ENOMEM, FBN_ETIMEOUT, FBN_ECUDA.  Synchronises the handle's stream. */
+int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap);
+
 /* fbn_learn_skeleton -- the first step of PC-stable (Algorithm 1): start from
  * the complete graph; at each depth d = 0, 1, ... snapshot the adjacency sets
  * a(V), test every remaining edge i<j against conditioning sets of size d

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/fbn.h"
+#include "fbn_gram.h"
 #include "fbn_launch.h"
 
 using namespace fbn;
@@ -138,6 +139,15 @@ struct fbn_handle {
     CiTestDesc* h_ci = nullptr;   // pinned
     double* h_ci_out = nullptr;   // pinned
     unsigned* h_status = nullptr; // pinned
+    // one-hot Gram (depth 0 on tensor cores)
+    int M = 0;                          // sum of arities
+    int Mp = 0;                         // M padded to the tile
+    long long K = 0;                    // samples padded to the stage width
+    int32_t* d_off = nullptr;           // [n] first one-hot row of each variable
+    uint8_t* d_E = nullptr;             // [Mp][K] E4M3 one-hot matrix
+    int32_t* d_G = nullptr;             // [Mp][Mp] INT32 Gram
+    int2* d_tiles = nullptr;
+    int n_tiles = 0;
     // results of the last skeleton
     bool learnt = false;
     std::vector<int32_t> sep_len;      // n*n, i<j entries
@@ -295,6 +305,44 @@ int check_status(fbn_handle* h, unsigned status)
     if (status & kStatusNumeric) return fail(h, FBN_ENUMERIC, "p-value iteration did not converge");
     if (status & kStatusSepPool) return fail(h, FBN_ECUDA, "separating-set pool overflow");
     if (status & kStatusEdges) return fail(h, FBN_ECUDA, "edge list overflow");
+    if (status & kStatusTimeout) return fail(h, FBN_ETIMEOUT, "a bounded device wait gave up");
+    return FBN_OK;
+}
+
+// Whether depth 0 of this handle runs as the one-hot Gram on tensor cores.
+bool use_gram(const fbn_handle* h, int k)
+{
+    if (k != 1) return false;   // batches: many small problems, histogram path
+    if (h->opt.depth0 == FBN_DEPTH0_GRAM) return true;
+    if (h->opt.depth0 == FBN_DEPTH0_HIST) return false;
+    return h->M >= 512 && h->N >= 8192;
+}
+
+// Build the one-hot matrix and its INT32 Gram (upper tile triangle) on the
+// handle's stream.  Buffers are allocated on first use and kept.
+int run_gram(fbn_handle* h, unsigned* d_status)
+{
+    cudaStream_t st = h->stream;
+    if (!h->d_E) {
+        h->Mp = gram_rows_padded(h->M);
+        h->K = gram_samples_padded(h->N);
+        CK(dalloc(&h->d_E, (size_t)h->Mp * h->K));
+        CK(dalloc(&h->d_G, (size_t)h->Mp * h->Mp));
+        const int T = h->Mp / 128;
+        std::vector<int2> tiles;
+        for (int a = 0; a < T; ++a)
+            for (int b = a; b < T; ++b) tiles.push_back(make_int2(a, b));
+        h->n_tiles = (int)tiles.size();
+        CK(dalloc(&h->d_tiles, tiles.size()));
+        CK(cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    // rows M..Mp stay zero; every row below M is rewritten each call
+    CK(cudaMemsetAsync(h->d_E + (size_t)h->M * h->K, 0, (size_t)(h->Mp - h->M) * h->K, st));
+    CK(launch_onehot(h->d_data, h->ld, h->n, (int)h->N, h->d_ar, h->d_off, h->d_E, h->K, st));
+    CK(cudaMemsetAsync(h->d_G, 0, (size_t)h->Mp * h->Mp * sizeof(int32_t), st));
+    CK(launch_gram(h->d_E, h->Mp, h->K, h->d_G, h->d_tiles, h->n_tiles, sms, d_status, st));
     return FBN_OK;
 }
 
@@ -342,6 +390,7 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
     const int gs = h->opt.group_size > 0 ? h->opt.group_size : kDefaultGs;
     const bool plain = h->opt.form == FBN_FORM_PLAIN;
     const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
+    const bool gram = !plain && use_gram(h, k);
     if (ws.crit_alpha != alpha) {
         CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
         ws.crit_alpha = alpha;
@@ -379,7 +428,20 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
 
         CK(cudaEventRecord(ws.kev[0], st));
         int group_used[2] = {0, 0};
-        for (int cls = 0; cls < 2; ++cls) {
+        const bool gram0 = d == 0 && gram;
+        if (gram0) {
+            rc = run_gram(h, &ws.d_ctr->status);
+            if (rc) return rc;
+            CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, 0};
+            for (int cls = 0; cls < 2; ++cls) {
+                if (Ec[cls] == 0) continue;
+                const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
+                CK(launch_pairs_decide(ws.edges + off, Ec[cls], ws.probs, h->d_G, h->Mp, h->d_off,
+                                       ws.min_accept + off, ct, alpha, &ws.d_ctr->tests, &ws.d_ctr->status, st));
+            }
+            launches += 5;
+        }
+        for (int cls = 0; cls < 2 && !gram0; ++cls) {
             if (Ec[cls] == 0) continue;
             const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
             PoolArgs a{};
@@ -580,6 +642,7 @@ void free_handle(fbn_handle* h)
     dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
+    dfree(h->d_off); dfree(h->d_E); dfree(h->d_G); dfree(h->d_tiles);
     if (h->h_ci) cudaFreeHost(h->h_ci);
     if (h->h_ci_out) cudaFreeHost(h->h_ci_out);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -699,6 +762,17 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         fail(h, FBN_EDATA, "value of variable %lld at sample %lld is >= its arity %d", v, s, (int)arities[v]);
         return bail(FBN_EDATA);
     }
+    {
+        std::vector<int32_t> off(n_vars);
+        int M = 0;
+        for (int v = 0; v < n_vars; ++v) {
+            off[v] = M;
+            M += arities[v];
+        }
+        h->M = M;
+        CKC(dalloc(&h->d_off, n_vars));
+        CKC(cudaMemcpy(h->d_off, off.data(), n_vars * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     ProblemDev P{};
     P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = n_vars; P.N = (int32_t)n_samples;
@@ -781,6 +855,24 @@ int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int
         }
     CK(cudaStreamSynchronize(h->stream));
     return FBN_OK;
+}
+
+int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
+{
+    if (!h) return FBN_EINVAL;
+    if (!counts) return fail(h, FBN_EINVAL, "counts is NULL");
+    const long long MM = (long long)h->M * h->M;
+    if (cap < MM) return fail(h, FBN_EINVAL, "cap %lld < M*M = %lld", (long long)cap, MM);
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+    int rc = run_gram(h, h->d_status);
+    if (rc) return rc;
+    CK(launch_symmetrize(h->d_G, h->Mp, h->M, h->stream));
+    CK(cudaMemcpy2DAsync(counts, (size_t)h->M * sizeof(int32_t), h->d_G, (size_t)h->Mp * sizeof(int32_t),
+                         (size_t)h->M * sizeof(int32_t), (size_t)h->M, cudaMemcpyDefault, h->stream));
+    CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return check_status(h, *h->h_status);
 }
 
 int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, int32_t cap)

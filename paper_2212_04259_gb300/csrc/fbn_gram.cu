@@ -1,0 +1,509 @@
+// fbn_gram.cu -- depth 0 of Algorithm 1 as a one-hot Gram product on the
+// fifth-generation tensor cores of sm_103a (tcgen05), all pairs at once.
+//
+// For every variable v and value x let e_{v,x} in {0,1}^N mark the samples
+// with V_v = x.  The depth-0 contingency table of the pair (i, j) is
+// N_ij(x, y) = <e_{i,x}, e_{j,y}>, so all n(n-1)/2 tables (Section IV-B: depth
+// zero tests every pair of the complete graph once) are blocks of the Gram
+// matrix E E^T of the one-hot matrix E [sum_v r_v][N].
+//
+// E is built in HBM as FP8 E4M3 (0 and 1 are exact).  The product runs on
+// tcgen05.mma.kind::f8f6f4 with FP32 accumulators in tensor memory; every
+// accumulation covers at most kChunk = 8192 samples, so each partial sum is an
+// integer below 2^13 and exact even if the accumulation kept only 14
+// significant bits.  Each chunk's 128x128 tile is added into an INT32 Gram in
+// global memory.  (tcgen05.mma.kind::i8 does not assemble for sm_103a with this
+// toolkit, hence FP8 0/1 operands.)
+//
+// Work unit = (upper-triangle tile pair, chunk of samples), chunk-major so
+// that the CTAs of a wave stream the same sample range and share it in L2.
+// CTA roles: warps 0-3 epilogue (TMEM -> registers -> coalesced INT32 atomic
+// adds), warp 4 TMA producer, warp 5 MMA issuer and TMEM owner.
+#include <algorithm>
+#include <cstdint>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include "fbn_device.cuh"
+#include "fbn_gram.h"
+
+namespace fbn {
+namespace {
+
+constexpr int kTile = 128;                           // rows of a tile = M = N of one MMA
+constexpr int kKSlice = 128;                         // samples (bytes) per pipeline stage
+constexpr int kChunk = 8192;                         // samples per exact accumulation
+constexpr int kSlicesPerChunk = kChunk / kKSlice;
+constexpr int kStages = 6;
+constexpr int kTileBytes = kTile * kKSlice;          // 16 KB
+constexpr int kStageBytes = 2 * kTileBytes;          // A + B
+constexpr int kGramThreads = 192;
+constexpr uint32_t kTmemCols = 256;                  // two 128-column FP32 accumulators
+constexpr unsigned kSpinLimit = 1u << 22;            // try_wait attempts before giving up
+constexpr int kStagePad = 33;                        // epilogue transpose tile row (ints)
+constexpr size_t kGramSmem = 1024 /*align*/ + (size_t)kStages * kStageBytes + 4 * 32 * kStagePad * 4 + 256;
+
+// Instruction descriptor of tcgen05.mma.kind::f8f6f4: D = FP32 (bits 4-5 = 1),
+// A = B = E4M3 (bits 7-9, 10-12 = 0), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity.  Gives
+// up (and raises the CTA's abort flag and the status bit) after kSpinLimit
+// attempts, or as soon as another role of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* status)
+{
+    for (unsigned it = 0; it < kSpinLimit; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    atomicOr(status, kStatusTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with
+// 128-byte swizzling: 8-row x 128-byte atoms, 1024 bytes between atoms
+// (stride byte offset), leading byte offset unused, version 1 (bits 46-47),
+// layout type SWIZZLE_128B = 2 (bits 61-63).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct GramArgs {
+    int32_t* G;           // [Mp][Mp] INT32 Gram, zeroed by the caller
+    const int2* tiles;    // upper-triangle tile pairs (ti <= tj)
+    int n_tiles;
+    int Mp;               // padded rows (multiple of 128)
+    int slices;           // padded samples / 128
+    int n_chunks;
+    unsigned* status;
+};
+
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant__ CUtensorMap tmap, GramArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    int* xpose = reinterpret_cast<int*>(smem + (size_t)kStages * kStageBytes);          // 4 x 32 x 33 ints
+    uint64_t* bars = reinterpret_cast<uint64_t*>(xpose + 4 * 32 * kStagePad);
+    uint64_t* full = bars;                 // [kStages] TMA -> MMA
+    uint64_t* empty = bars + kStages;      // [kStages] MMA -> TMA
+    uint64_t* acc_full = bars + 2 * kStages;       // [2] MMA -> epilogue
+    uint64_t* acc_empty = bars + 2 * kStages + 2;  // [2] epilogue -> MMA
+    uint64_t* drain = bars + 2 * kStages + 4;      // MMA completion before teardown
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* issued = reinterpret_cast<int*>(tmem_slot + 2);   // [kStages], producer thread only
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int U = g.n_tiles * g.n_chunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+            issued[s] = 0;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 1);
+            mbar_init(smem_u32(&acc_empty[b]), 4);   // one arrive per epilogue warp
+        }
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int u = blockIdx.x; u < U && !*abort_flag; u += gridDim.x) {
+                const int c = u / g.n_tiles;
+                const int2 t = g.tiles[u - c * g.n_tiles];
+                const int kb0 = c * kSlicesPerChunk;
+                const int kb1 = min(kb0 + kSlicesPerChunk, g.slices);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag, g.status)) break;
+                    const uint32_t fb = smem_u32(&full[stage]);
+                    const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
+                    mbar_expect_tx(fb, kStageBytes);
+                    tma_load_2d(a, &tmap, fb, kb * kKSlice, t.x * kTile);
+                    tma_load_2d(a + kTileBytes, &tmap, fb, kb * kKSlice, t.y * kTile);
+                    issued[stage] += 1;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer (one thread)
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
+                const int c = u / g.n_tiles;
+                const int kb0 = c * kSlicesPerChunk;
+                const int kb1 = min(kb0 + kSlicesPerChunk, g.slices);
+                if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag, g.status)) break;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * kTile);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag, g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
+                    const uint64_t da = smem_desc(a), db = smem_desc(a + kTileBytes);
+#pragma unroll
+                    for (int k = 0; k < kKSlice / 32; ++k)   // 32 E4M3 values = 32 bytes of K per MMA
+                        mma_f8(d_tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), (kb > kb0 || k > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty[stage]));
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&acc_full[acc]));
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            // every MMA this thread issued has finished before TMEM is released
+            mma_commit(smem_u32(drain));
+            mbar_wait(smem_u32(drain), 0, abort_flag, g.status);
+        }
+    } else {
+        // ---------------- epilogue: warps 0-3, TMEM lanes 32w .. 32w+31
+        int* xp = xpose + warp * 32 * kStagePad;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int u = blockIdx.x; u < U; u += gridDim.x) {
+            const int c = u / g.n_tiles;
+            const int2 t = g.tiles[u - c * g.n_tiles];
+            if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag, g.status)) break;
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kTile);
+            const long long row0 = (long long)t.x * kTile + warp * 32;
+            for (int j0 = 0; j0 < kTile; j0 += 32) {
+                uint32_t v[32];
+                tmem_ld32(base + (uint32_t)j0, v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) xp[lane * kStagePad + q] = __float2int_rn(__uint_as_float(v[q]));
+                __syncwarp();
+                int32_t* dst = g.G + row0 * g.Mp + (long long)t.y * kTile + j0 + lane;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const int val = xp[r * kStagePad + lane];
+                    if (val) atomicAdd(dst + (long long)r * g.Mp, val);
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+            acc ^= 1;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    __syncthreads();
+    if (warp == 4 && lane == 0) {
+        // no TMA write may land after the CTA exits: wait for the last load of
+        // every stage (immediate unless a role gave up)
+        for (int s = 0; s < kStages; ++s)
+            if (issued[s] > 0) {
+                for (unsigned it = 0; it < kSpinLimit; ++it)
+                    if (mbar_try(smem_u32(&full[s]), (uint32_t)((issued[s] - 1) & 1))) break;
+            }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// One-hot matrix E: row off_v + x holds 0x38 (E4M3 1.0) where V_v = x, else
+// 0; samples at or beyond N (the padding of the store) are 0 for every row.
+__global__ void k_onehot(const uint8_t* __restrict__ data, long long ld, int n, int N, const uint8_t* __restrict__ ar,
+                         const int32_t* __restrict__ off, uint8_t* __restrict__ E, long long K)
+{
+    const int v = blockIdx.y;
+    const int r = ar[v];
+    const uint4* row = reinterpret_cast<const uint4*>(data + (long long)v * ld);
+    const long long nvec = K / 16;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long long)gridDim.x * blockDim.x) {
+        uint4 w = row[q];
+        const long long s0 = q * 16;
+        uint32_t keep[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // byte mask of samples below N
+            uint32_t m = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (s0 + 4 * k + b < N) m |= 0xFFu << (8 * b);
+            keep[k] = m;
+        }
+        for (int x = 0; x < r; ++x) {
+            const uint32_t rep = 0x01010101u * (uint32_t)x;
+            uint4 o;
+            o.x = __vcmpeq4(w.x, rep) & 0x38383838u & keep[0];
+            o.y = __vcmpeq4(w.y, rep) & 0x38383838u & keep[1];
+            o.z = __vcmpeq4(w.z, rep) & 0x38383838u & keep[2];
+            o.w = __vcmpeq4(w.w, rep) & 0x38383838u & keep[3];
+            reinterpret_cast<uint4*>(E + (long long)(off[v] + x) * K)[q] = o;
+        }
+    }
+}
+
+// Depth-0 decisions from the Gram: one thread per edge (i<j) of the list.
+__global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long E, const ProblemDev* __restrict__ probs,
+                               const int32_t* __restrict__ G, int Mp, const int32_t* __restrict__ off,
+                               unsigned long long* __restrict__ min_accept, CritTableDev crit, double alpha,
+                               unsigned long long* tests, unsigned* status)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const EdgeWork w = edges[e];
+    const ProblemDev& P = probs[w.prob];
+    const int rx = P.ar[w.i], ry = P.ar[w.j];
+    const int32_t* T = G + (long long)off[w.i] * Mp + off[w.j];
+    int rs[kMaxArityPairs], cs[kMaxArityPairs];
+    int tot = 0;
+    for (int x = 0; x < rx; ++x) rs[x] = 0;
+    for (int y = 0; y < ry; ++y) cs[y] = 0;
+    for (int x = 0; x < rx; ++x)
+        for (int y = 0; y < ry; ++y) {
+            const int nxy = T[(long long)x * Mp + y];
+            rs[x] += nxy;
+            cs[y] += nxy;
+            tot += nxy;
+        }
+    // terms with FP32 logs summed in FP64 (each term within 3.2e-7 of its
+    // magnitude); exact FP64 only when crit lies inside the error band
+    const long long df = (long long)(rx - 1) * (ry - 1);
+    const double c = crit_get(crit, df, alpha, status);
+    double acc = 0.0, mag = 0.0;
+    for (int x = 0; x < rx; ++x)
+        for (int y = 0; y < ry; ++y) {
+            const int n = T[(long long)x * Mp + y];
+            if (n == 0) continue;
+            const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
+            const float fb = (float)b;
+            const float delta = (float)(a - b) / fb;
+            const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
+            acc += (double)((float)n * L);
+            mag += fabs((double)((float)n * L));
+        }
+    double g2 = 2.0 * acc;
+    const double err = 2.0 * 2.0 * 3.2e-7 * mag * 1.0001 + 1e-9;
+    bool accept;
+    if (g2 + err < c) {
+        accept = true;
+    } else if (g2 - err >= c) {
+        accept = false;
+    } else {
+        double ex = 0.0;
+        for (int x = 0; x < rx; ++x)
+            for (int y = 0; y < ry; ++y) {
+                const int n = T[(long long)x * Mp + y];
+                if (n == 0) continue;
+                const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
+                ex += (double)n * log1p((double)(a - b) / (double)b);
+            }
+        accept = 2.0 * ex < c;
+    }
+    if (accept) min_accept[e] = 0;
+    atomicAdd(tests, 1ULL);
+}
+
+// Mirror the upper block triangle into the lower one (row < col -> col, row).
+__global__ void k_symmetrize(int32_t* G, int Mp, int M)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= (long long)M * M) return;
+    const int r = (int)(k / M), c = (int)(k - (long long)r * M);
+    if (r > c) G[(long long)r * Mp + c] = G[(long long)c * Mp + r];
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+size_t gram_smem_bytes() { return kGramSmem; }
+
+int gram_rows_padded(int M) { return (M + kTile - 1) / kTile * kTile; }
+
+long long gram_samples_padded(long long N) { return (N + kKSlice - 1) / kKSlice * kKSlice; }
+
+cudaError_t launch_onehot(const uint8_t* data, long long ld, int n, int N, const uint8_t* ar, const int32_t* off,
+                          uint8_t* E, long long K, cudaStream_t st)
+{
+    dim3 grid((unsigned)std::min<long long>((K / 16 + 255) / 256, 64), (unsigned)n);
+    k_onehot<<<grid, 256, 0, st>>>(data, ld, n, N, ar, off, E, K);
+    return cudaGetLastError();
+}
+
+// Gram of the one-hot matrix E [Mp][K] (K a multiple of 128) into G [Mp][Mp]
+// (upper tile triangle; G must be zero).  tiles: device array of the
+// Mp/128 (Mp/128 + 1)/2 tile pairs.
+cudaError_t launch_gram(const uint8_t* E, int Mp, long long K, int32_t* G, const int2* tiles, int n_tiles,
+                        int num_sms, unsigned* status, cudaStream_t st)
+{
+    auto encode = encode_fn();
+    if (!encode) return cudaErrorNotSupported;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Mp};
+    cuuint64_t strides[1] = {(cuuint64_t)K};
+    cuuint32_t box[2] = {(cuuint32_t)kKSlice, (cuuint32_t)kTile};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(E), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    GramArgs g;
+    g.G = G;
+    g.tiles = tiles;
+    g.n_tiles = n_tiles;
+    g.Mp = Mp;
+    g.slices = (int)(K / kKSlice);
+    g.n_chunks = (g.slices + kSlicesPerChunk - 1) / kSlicesPerChunk;
+    g.status = status;
+    cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem);
+    if (e != cudaSuccess) return e;
+    const int units = n_tiles * g.n_chunks;
+    const int grid = units < num_sms ? units : num_sms;
+    k_gram<<<grid, kGramThreads, kGramSmem, st>>>(map, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_decide(const EdgeWork* edges, long long E, const ProblemDev* probs, const int32_t* G,
+                                int Mp, const int32_t* off, unsigned long long* min_accept, const CritTableDev& crit,
+                                double alpha, unsigned long long* tests, unsigned* status, cudaStream_t st)
+{
+    if (E == 0) return cudaSuccess;
+    k_pairs_decide<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(edges, E, probs, G, Mp, off, min_accept, crit, alpha,
+                                                                tests, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(int32_t* G, int Mp, int M, cudaStream_t st)
+{
+    const long long n = (long long)M * M;
+    k_symmetrize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(G, Mp, M);
+    return cudaGetLastError();
+}
+
+}  // namespace fbn

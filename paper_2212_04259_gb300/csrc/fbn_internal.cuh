@@ -21,6 +21,8 @@ constexpr unsigned kStatusTooBig = 1u;    // table over kMaxCells or scratch too
 constexpr unsigned kStatusNumeric = 2u;   // p-value iteration hit its cap
 constexpr unsigned kStatusSepPool = 4u;   // separating-set pool overflow
 constexpr unsigned kStatusEdges = 8u;     // edge list overflow
+constexpr unsigned kStatusTimeout = 16u;  // a bounded device wait gave up
+constexpr int kMaxArityPairs = 256;       // arity bound of the depth-0 pair epilogue
 
 // One learning problem (one data set).  Arrays are device pointers.
 struct ProblemDev {

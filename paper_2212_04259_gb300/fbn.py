@@ -25,7 +25,7 @@ MAX_DEPTHS = 64
 # Every symbol include/fbn.h declares.
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_get_stats",
-           "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc")
+           "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts")
 
 
 class FbnError(RuntimeError):
@@ -83,6 +83,8 @@ def lib():
         L.fbn_last_error.argtypes = [p]
         L.fbn_destroy.restype = None
         L.fbn_destroy.argtypes = [p]
+        L.fbn_pairwise_counts.restype = C.c_int
+        L.fbn_pairwise_counts.argtypes = [p, p, i64]
         L.fbn_ci_test_noalloc.restype = C.c_int
         L.fbn_ci_test_noalloc.argtypes = [p, i64, i32, i64, p, i32, i32, p, i32, p, p, p]
         _lib = L
@@ -183,6 +185,16 @@ def fbn_ci_table(h: Handle, x: int, y: int, z=(), cells=None) -> np.ndarray:
         cells = max(1, min(cells, 1 << 25))
     out = np.zeros(cells, dtype=np.int32)
     _check(lib().fbn_ci_table(h.ptr, x, y, _ptr(za) if len(za) else None, len(za), _ptr(out), cells), h)
+    return out
+
+
+def fbn_pairwise_counts(h: Handle, out=None) -> np.ndarray:
+    """All depth-0 pair tables as the symmetric int32 [M][M] one-hot Gram
+    (M = sum of arities); out may be a preallocated host or device buffer."""
+    M = int(sum(int(a) for a in h.arities))
+    if out is None:
+        out = np.zeros((M, M), dtype=np.int32)
+    _check(lib().fbn_pairwise_counts(h.ptr, _ptr(out), M * M), h)
     return out
 
 
