@@ -57,7 +57,7 @@ def load_workload(name):
 
 
 def workload_config(name, w, args):
-    cfg = {"workload": name, "form": args.form, "group_size": args.gs or 4,
+    cfg = {"workload": name, "form": args.form, "group_size": args.gs or 1,
            "l2": "flushed by a 256 MB device write before each timed step"}
     if w["kind"] == "single":
         n, N = w["data"].shape
@@ -282,63 +282,85 @@ def main():
         ms = float(t.item())
     value = world * tests / (ms / 1e3)
 
-    # roofline of the CI-test kernel: algorithmic sample bytes (d+2) N per oracle-equivalent test
+    # rooflines.  Histogram test kernels (the work pool): algorithmic sample
+    # bytes (d + 2) N per oracle-equivalent test over their CUDA-event time,
+    # against the measured HBM copy bandwidth.  Depth 0 on the one-hot Gram:
+    # algorithmic FLOPs 2 * M^2 * N / 2 (upper triangle, M = sum of arities)
+    # over the Gram kernel's time, against the FP8 dense peak (the measured
+    # bf16 peak times the nominal FP8/BF16 ratio of 2).
     if w["kind"] == "single":
         Ns = [w["data"].shape[1]]
     else:
         Ns = [d.shape[1] for d, _ in w["probs"]]
     meanN = sum(Ns) / len(Ns)
-    alg_bytes = sum(c * (d + 2) * meanN for d, c in enumerate(st["tests_oracle"]))
-    test_ms = sum(stats_acc["test_ms"]) / args.steps
+    gram_used = st["gram_ms"] > 0
+    pool_depths = [d for d in range(st["depths"]) if not (gram_used and d == 0)]
+    alg_bytes = sum(st["tests_oracle"][d] * (d + 2) * meanN for d in pool_depths)
+    test_ms = sum(stats_acc["test_ms"][d] for d in pool_depths) / args.steps
     achieved = alg_bytes / (test_ms / 1e3) / 1e9 if test_ms > 0 else 0.0
     try:
         peaks = json.load(open(PEAKS))
         peak, peak_src = float(peaks["hbm_gbs"]), "of measured"
+        bf16 = float(peaks["bf16_tflops"])
+        fp8_peak, fp8_src = 2.0 * bf16, "of measured (bf16 burst x nominal fp8/bf16 ratio 2)"
     except Exception:
         peak, peak_src = FALLBACK_HBM_GBS, "of fallback"
+        fp8_peak, fp8_src = 2.0 * 1900.0, "of fallback (bf16 x 2)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_src, "kernel": "k_pool<32>+k_pool<256>" if args.form == "pool" else "k_plain",
-                "kernel_ms_per_step": test_ms, "algorithmic_bytes_per_step": alg_bytes}
+                "traffic": None, "peak_source": peak_src,
+                "kernel": "k_pool<G> (depths %s)" % ",".join(str(d) for d in pool_depths) if args.form == "pool"
+                else "k_plain", "kernel_ms_per_step": test_ms, "algorithmic_bytes_per_step": alg_bytes}
+    roofline_gram = None
+    if gram_used:
+        M, K = st["gram_rows"], meanN
+        flops = float(M) * M * K            # 2 M^2 N / 2
+        gms = st["gram_ms"]
+        tf = flops / (gms / 1e3) / 1e12
+        roofline_gram = {"bound": "tensor", "achieved": tf, "peak": fp8_peak, "unit": "TFLOP/s",
+                         "frac": tf / fp8_peak, "traffic": None, "peak_source": fp8_src, "kernel": "k_gram",
+                         "kernel_ms": gms, "algorithmic_flops": flops}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies
+    # the samples from pinned host memory into the handle (fbn_update_data),
+    # learns the skeleton into a pinned host adjacency and exports the
+    # separating sets to host arrays
     e2e = None
-    if True:  # every rank measures its own replica
+    if w["kind"] == "single":
+        host = torch.from_numpy(w["data"]).pin_memory()
+        n = w["data"].shape[0]
+        adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
+        he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local)
+        F.fbn_set_stream(he, stream)
+        hs_e2e, hosts, adjs_host = [he], [host], [adj_host]
+    else:
+        hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
+        adjs_host = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8).pin_memory() for d, _ in w["probs"]]
+        hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local)
+                  for hh, (_, a) in zip(hosts, w["probs"])]
+        F.fbn_set_stream(hs_e2e[0], stream)
+    e2e_ms, d2h = [], 0
+    for it in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for hh, hd in zip(hs_e2e, hosts):
+            F.fbn_update_data(hh, hd)
         if w["kind"] == "single":
-            host = torch.from_numpy(w["data"]).pin_memory()
-            n = w["data"].shape[0]
-            adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
-            e2e_ms = []
-            d2h = 0
-            for _ in range(args.e2e_steps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                h2 = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local)
-                F.fbn_learn_skeleton(h2, w["alpha"], w["max_depth"], adj_out=adj_host)
-                seps = F.fbn_export_sepsets(h2)
-                F.fbn_destroy(h2)
-                torch.cuda.synchronize()
-                e2e_ms.append(1e3 * (time.perf_counter() - t0))
-                d2h = n * n + n * n * 12 + 4 * sum(len(s) for s in seps.values())
-            e2e_v = tests / (statistics.median(e2e_ms) / 1e3)
-            e2e = {"value": world * e2e_v, "unit": "tests/s", "h2d_bytes_per_step": int(host.numel() + n),
-                   "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.median(e2e_ms)}
+            F.fbn_learn_skeleton(hs_e2e[0], w["alpha"], w["max_depth"], adj_out=adjs_host[0])
         else:
-            hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
-            e2e_ms = []
-            for _ in range(args.e2e_steps):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                hs = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local)
-                      for hh, (_, a) in zip(hosts, w["probs"])]
-                F.fbn_learn_skeleton_batch(hs, w["alpha"], w["max_depth"])
-                for hh in hs:
-                    F.fbn_destroy(hh)
-                torch.cuda.synchronize()
-                e2e_ms.append(1e3 * (time.perf_counter() - t0))
-            nn = sum(d.shape[0] ** 2 for d, _ in w["probs"])
-            e2e = {"value": world * tests / (statistics.median(e2e_ms) / 1e3), "unit": "tests/s",
-                   "h2d_bytes_per_step": int(sum(h.numel() for h in hosts)), "d2h_bytes_per_step": int(13 * nn),
-                   "ms_per_step": statistics.median(e2e_ms)}
+            F.fbn_learn_skeleton_batch(hs_e2e, w["alpha"], w["max_depth"], adj_out=adjs_host)
+        members = 0
+        for hh in hs_e2e:
+            _, _, mem = F.fbn_export_sepsets(hh, as_dict=False)
+            members += len(mem)
+        torch.cuda.synchronize()
+        if it > 0:   # the first pass warms the handle
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        d2h = sum(hh.n * hh.n * 13 for hh in hs_e2e) + 4 * members
+    e2e = {"value": world * tests / (statistics.median(e2e_ms) / 1e3), "unit": "tests/s",
+           "h2d_bytes_per_step": int(sum(hh.numel() for hh in hosts)), "d2h_bytes_per_step": int(d2h),
+           "ms_per_step": statistics.median(e2e_ms)}
+    for hh in hs_e2e:
+        F.fbn_destroy(hh)
 
     # the plain edge-level GPU form on the same workload, for comparison
     plain = None
@@ -374,6 +396,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
                 "config": workload_config(name, w, args), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(st["launches"]) * args.steps, "roofline": roofline,
+                "roofline_gram": roofline_gram,
                 "cpu_baseline": cpu, "plain_form": plain,
                 "tests_per_step": {"oracle_equivalent": tests, "executed": sum(st["tests"]),
                                    "per_depth_oracle": st["tests_oracle"]},

@@ -44,7 +44,7 @@ extern "C" {
 
 typedef struct fbn_options {
     int32_t form;        /* FBN_FORM_POOL (default) or FBN_FORM_PLAIN */
-    int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default */
+    int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default (1) */
     int32_t depth0;      /* FBN_DEPTH0_* */
     int32_t device;      /* CUDA device ordinal; -1 = the current device */
     int32_t group_threads; /* threads per CI test in the pool: 32, 64, 128 or 256; 0 = chosen per depth */
@@ -62,7 +62,10 @@ typedef struct fbn_stats {
     int64_t tests_oracle[FBN_MAX_DEPTHS];   /* tests the sequential Algorithm 1 runs (gs = 1) */
     int64_t removed[FBN_MAX_DEPTHS];        /* edges removed at depth d */
     double  ms[FBN_MAX_DEPTHS];             /* device time of depth d (CUDA events) */
-    double  test_ms[FBN_MAX_DEPTHS];        /* device time of depth d's CI-test kernel */
+    double  test_ms[FBN_MAX_DEPTHS];        /* device time of depth d's CI-test kernels */
+    double  gram_ms;                        /* device time of the one-hot Gram (0 if not used) */
+    int64_t gram_rows;                      /* M = sum of arities, when the Gram ran */
+    int64_t gram_samples;                   /* padded samples of the Gram */
 } fbn_stats;
 
 typedef struct fbn_handle fbn_handle;
@@ -81,6 +84,13 @@ typedef struct fbn_handle fbn_handle;
  * fails before a handle exists, fbn_last_error(NULL) gives the reason. */
 int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples,
                const uint8_t* arities, const fbn_options* opt, fbn_handle** out);
+
+/* fbn_update_data -- replace the handle's samples with a new data set of the
+ * same shape (n_vars x n_samples, same arities), host or device memory, as in
+ * fbn_create; keeps every device buffer.  Results of earlier calls are
+ * dropped.  Errors: FBN_EINVAL, FBN_EDATA (a value >= its arity; the handle's
+ * data is then undefined until the next successful update), FBN_ECUDA. */
+int fbn_update_data(fbn_handle* h, const uint8_t* data);
 
 /* fbn_set_stream -- run the handle's work on a caller-owned cudaStream_t
  * (passed as void*; NULL selects the handle's own stream).  The stream must
@@ -127,7 +137,8 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap);
  *   adj_out : uint8 [n][n], host or device, receives the symmetric 0/1
  *             adjacency of the skeleton (zero diagonal).  Nullable.
  * Separating sets stay in the handle until the next call or fbn_destroy; read
- * them with fbn_get_sepset / fbn_export_sepsets.
+ * them with fbn_get_sepset / fbn_export_sepsets (the first such read copies
+ * them from the device).
  * Errors: FBN_EINVAL (alpha outside (0, 1), max_depth < -1), FBN_ETOOBIG,
  * FBN_ENOMEM, FBN_ENUMERIC, FBN_ECUDA. */
 int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* adj_out);

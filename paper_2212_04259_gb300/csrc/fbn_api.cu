@@ -23,7 +23,7 @@ thread_local std::string g_create_error;
 
 constexpr size_t kSmemBytes = 108 * 1024;     // dynamic shared memory of a CTA test group (2 CTAs / SM)
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
-constexpr int kDefaultGs = 4;
+constexpr int kDefaultGs = 1;
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
 
 template <typename T>
@@ -92,7 +92,7 @@ struct Workspace {
     double* crit_vals = nullptr;
     double crit_alpha = -1.0;
     cudaEvent_t ev[FBN_MAX_DEPTHS + 1] = {};
-    cudaEvent_t kev[2] = {};
+    cudaEvent_t kev[4] = {};
     bool events = false;
 
     void release()
@@ -150,6 +150,8 @@ struct fbn_handle {
     int n_tiles = 0;
     // results of the last skeleton
     bool learnt = false;
+    bool sep_pending = false;           // separating sets still only on the device
+    unsigned long long sep_pool_used = 0;
     std::vector<int32_t> sep_len;      // n*n, i<j entries
     std::vector<int64_t> sep_off;      // n*n offsets into sep_members
     std::vector<int32_t> sep_members;
@@ -320,7 +322,7 @@ bool use_gram(const fbn_handle* h, int k)
 
 // Build the one-hot matrix and its INT32 Gram (upper tile triangle) on the
 // handle's stream.  Buffers are allocated on first use and kept.
-int run_gram(fbn_handle* h, unsigned* d_status)
+int run_gram(fbn_handle* h, unsigned* d_status, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
 {
     cudaStream_t st = h->stream;
     if (!h->d_E) {
@@ -342,7 +344,41 @@ int run_gram(fbn_handle* h, unsigned* d_status)
     CK(cudaMemsetAsync(h->d_E + (size_t)h->M * h->K, 0, (size_t)(h->Mp - h->M) * h->K, st));
     CK(launch_onehot(h->d_data, h->ld, h->n, (int)h->N, h->d_ar, h->d_off, h->d_E, h->K, st));
     CK(cudaMemsetAsync(h->d_G, 0, (size_t)h->Mp * h->Mp * sizeof(int32_t), st));
+    if (ev0) CK(cudaEventRecord(ev0, st));
     CK(launch_gram(h->d_E, h->Mp, h->K, h->d_G, h->d_tiles, h->n_tiles, sms, d_status, st));
+    if (ev1) CK(cudaEventRecord(ev1, st));
+    return FBN_OK;
+}
+
+// Copy the separating sets of h (in the pool of workspace ws) to the host,
+// as CSR rows per removed pair.
+int materialize_sepsets(fbn_handle* h, Workspace& ws)
+{
+    if (!h->sep_pending) return FBN_OK;
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    const size_t nn = (size_t)h->n * h->n;
+    std::vector<int32_t> pool(h->sep_pool_used);
+    std::vector<int32_t> len(nn);
+    std::vector<int64_t> off(nn);
+    if (h->sep_pool_used)
+        CK(cudaMemcpyAsync(pool.data(), ws.sep_pool, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(len.data(), h->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(off.data(), h->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    h->sep_len.assign(nn, -1);
+    h->sep_off.assign(nn, 0);
+    h->sep_members.clear();
+    for (int i = 0; i < h->n; ++i)
+        for (int j = i + 1; j < h->n; ++j) {
+            const size_t ij = (size_t)i * h->n + j;
+            const int32_t L = len[ij];
+            if (L < 0) continue;
+            h->sep_len[ij] = L;
+            h->sep_off[ij] = (int64_t)h->sep_members.size();
+            for (int t = 0; t < L; ++t) h->sep_members.push_back(pool[(size_t)off[ij] + t]);
+        }
+    h->sep_pending = false;
     return FBN_OK;
 }
 
@@ -430,7 +466,7 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
         int group_used[2] = {0, 0};
         const bool gram0 = d == 0 && gram;
         if (gram0) {
-            rc = run_gram(h, &ws.d_ctr->status);
+            rc = run_gram(h, &ws.d_ctr->status, ws.kev[2], ws.kev[3]);
             if (rc) return rc;
             CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, 0};
             for (int cls = 0; cls < 2; ++cls) {
@@ -526,6 +562,13 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
         CK(cudaEventElapsedTime(&ms, ws.ev[d], ws.ev[d + 1]));
         CK(cudaEventElapsedTime(&kms, ws.kev[0], ws.kev[1]));
         stats.test_ms[d] = kms;
+        if (gram0) {
+            float gms = 0.f;
+            CK(cudaEventElapsedTime(&gms, ws.kev[2], ws.kev[3]));
+            stats.gram_ms = gms;
+            stats.gram_rows = h->M;
+            stats.gram_samples = h->K;
+        }
         stats.depths = d + 1;
         stats.edges[d] = E;
         stats.tests[d] = (int64_t)ws.h_ctr->tests;
@@ -536,32 +579,17 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
     }
 
     stats.launches = launches;
-    // Bring the separating sets of every problem to the host.
-    std::vector<int32_t> pool(sep_used);
-    if (sep_used)
-        CK(cudaMemcpyAsync(pool.data(), ws.sep_pool, sep_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     for (int p = 0; p < k; ++p) {
-        fbn_handle* q = hs[p];
-        const size_t nn = (size_t)q->n * q->n;
-        std::vector<int32_t> len(nn);
-        std::vector<int64_t> off(nn);
-        CK(cudaMemcpyAsync(len.data(), q->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(off.data(), q->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        q->sep_len.assign(nn, -1);
-        q->sep_off.assign(nn, 0);
-        q->sep_members.clear();
-        for (int i = 0; i < q->n; ++i)
-            for (int j = i + 1; j < q->n; ++j) {
-                const size_t ij = (size_t)i * q->n + j;
-                const int32_t L = len[ij];
-                if (L < 0) continue;
-                q->sep_len[ij] = L;
-                q->sep_off[ij] = (int64_t)q->sep_members.size();
-                for (int t = 0; t < L; ++t) q->sep_members.push_back(pool[(size_t)off[ij] + t]);
-            }
-        q->stats = stats;
-        q->learnt = true;
+        hs[p]->stats = stats;
+        hs[p]->learnt = true;
+        hs[p]->sep_pending = true;
+        hs[p]->sep_pool_used = sep_used;
+    }
+    if (k == 1) return FBN_OK;   // a single problem's sets stay on the device until asked for
+    // a batch shares the first handle's pool: bring every problem's sets over now
+    for (int p = 0; p < k; ++p) {
+        rc = materialize_sepsets(hs[p], ws);
+        if (rc) return rc;
     }
     return FBN_OK;
 }
@@ -784,6 +812,33 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     return FBN_OK;
 }
 
+int fbn_update_data(fbn_handle* h, const uint8_t* data)
+{
+    if (!h) return FBN_EINVAL;
+    if (!data) return fail(h, FBN_EINVAL, "data is NULL");
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    h->learnt = false;
+    h->sep_pending = false;
+    CK(cudaMemcpy2DAsync(h->d_data, h->ld, data, h->N, h->N, h->n, cudaMemcpyDefault, st));
+    unsigned long long* bad = (unsigned long long*)h->d_ci_out;   // 8 bytes of scratch
+    CK(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st));
+    dim3 grid((unsigned)std::min<long long>((h->N + 255) / 256, 64), h->n);
+    k_validate<<<grid, 256, 0, st>>>(h->d_data, h->ld, h->n, h->N, h->d_ar, bad);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_status, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    unsigned long long first_bad;
+    std::memcpy(&first_bad, h->h_status, sizeof first_bad);
+    if (first_bad != ~0ULL) {
+        const long long v = (long long)(first_bad / (unsigned long long)h->N);
+        const long long smp = (long long)(first_bad % (unsigned long long)h->N);
+        return fail(h, FBN_EDATA, "value of variable %lld at sample %lld is >= its arity %d", v, smp,
+                    (int)h->h_ar[v]);
+    }
+    return FBN_OK;
+}
+
 int fbn_set_stream(fbn_handle* h, void* stream)
 {
     if (!h) return FBN_EINVAL;
@@ -824,6 +879,7 @@ int fbn_ci_table(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t 
 int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* adj_out)
 {
     if (!h) return FBN_EINVAL;
+    h->sep_pending = false;
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
     if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
     h->learnt = false;
@@ -842,6 +898,7 @@ int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int
         if (!hs[p]) return fail(h, FBN_EINVAL, "handle %d is NULL", p);
         if (hs[p]->device != h->device) return fail(h, FBN_EINVAL, "handle %d is on another device", p);
         hs[p]->learnt = false;
+        hs[p]->sep_pending = false;
     }
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
     if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
@@ -875,9 +932,14 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
     return check_status(h, *h->h_status);
 }
 
-int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, int32_t cap)
+int32_t fbn_get_sepset(const fbn_handle* hc, int32_t i, int32_t j, int32_t* buf, int32_t cap)
 {
-    if (!h || !h->learnt) return FBN_EINVAL;
+    if (!hc || !hc->learnt) return FBN_EINVAL;
+    fbn_handle* h = const_cast<fbn_handle*>(hc);   // the host copy is a cache of device results
+    if (h->sep_pending) {
+        const int rc = materialize_sepsets(h, h->ws);
+        if (rc) return rc;
+    }
     if (i < 0 || j < 0 || i >= h->n || j >= h->n || i == j) return FBN_EINVAL;
     if (i > j) std::swap(i, j);
     const size_t ij = (size_t)i * h->n + j;
@@ -888,10 +950,15 @@ int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, 
     return L;
 }
 
-int fbn_export_sepsets(const fbn_handle* h, int64_t* n_removed, int64_t* n_members, int32_t* pairs,
+int fbn_export_sepsets(const fbn_handle* hc, int64_t* n_removed, int64_t* n_members, int32_t* pairs,
                        int64_t* offsets, int32_t* members)
 {
-    if (!h || !h->learnt || !n_removed || !n_members) return FBN_EINVAL;
+    if (!hc || !hc->learnt || !n_removed || !n_members) return FBN_EINVAL;
+    fbn_handle* h = const_cast<fbn_handle*>(hc);   // the host copy is a cache of device results
+    if (h->sep_pending) {
+        const int rc = materialize_sepsets(h, h->ws);
+        if (rc) return rc;
+    }
     int64_t nr = 0, nm = 0;
     for (int i = 0; i < h->n; ++i)
         for (int j = i + 1; j < h->n; ++j) {

@@ -25,7 +25,8 @@ MAX_DEPTHS = 64
 # Every symbol include/fbn.h declares.
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_get_stats",
-           "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts")
+           "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
+           "fbn_update_data")
 
 
 class FbnError(RuntimeError):
@@ -43,7 +44,8 @@ class Stats(C.Structure):
     _fields_ = [("depths", C.c_int32), ("reserved", C.c_int32), ("launches", C.c_int64),
                 ("edges", C.c_int64 * MAX_DEPTHS), ("tests", C.c_int64 * MAX_DEPTHS),
                 ("tests_oracle", C.c_int64 * MAX_DEPTHS), ("removed", C.c_int64 * MAX_DEPTHS),
-                ("ms", C.c_double * MAX_DEPTHS), ("test_ms", C.c_double * MAX_DEPTHS)]
+                ("ms", C.c_double * MAX_DEPTHS), ("test_ms", C.c_double * MAX_DEPTHS),
+                ("gram_ms", C.c_double), ("gram_rows", C.c_int64), ("gram_samples", C.c_int64)]
 
 
 _lock = threading.Lock()
@@ -83,6 +85,8 @@ def lib():
         L.fbn_last_error.argtypes = [p]
         L.fbn_destroy.restype = None
         L.fbn_destroy.argtypes = [p]
+        L.fbn_update_data.restype = C.c_int
+        L.fbn_update_data.argtypes = [p, p]
         L.fbn_pairwise_counts.restype = C.c_int
         L.fbn_pairwise_counts.argtypes = [p, p, i64]
         L.fbn_ci_test_noalloc.restype = C.c_int
@@ -149,6 +153,14 @@ def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-
     rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
     _check(rc)
     return Handle(out, n, N, ar.copy())
+
+
+def fbn_update_data(h: Handle, data) -> None:
+    """Replace the samples (same shape) from numpy or a torch host/device tensor."""
+    data, shape = _as_u8_2d(data)
+    if tuple(shape) != (h.n, h.n_samples):
+        raise ValueError("data must keep the handle's shape")
+    _check(lib().fbn_update_data(h.ptr, _ptr(data)), h)
 
 
 def fbn_set_stream(h: Handle, stream) -> None:
@@ -228,8 +240,9 @@ def fbn_get_sepset(h: Handle, i: int, j: int):
     return tuple(int(v) for v in buf[:k])
 
 
-def fbn_export_sepsets(h: Handle) -> dict:
-    """{(i, j): tuple(S)} for every removed pair i < j."""
+def fbn_export_sepsets(h: Handle, as_dict: bool = True):
+    """{(i, j): tuple(S)} for every removed pair i < j; with as_dict=False the
+    CSR arrays (pairs int32 [R][2], offsets int64 [R+1], members int32)."""
     nr, nm = C.c_int64(), C.c_int64()
     L = lib()
     _check(L.fbn_export_sepsets(h.ptr, C.byref(nr), C.byref(nm), None, None, None), h)
@@ -237,6 +250,8 @@ def fbn_export_sepsets(h: Handle) -> dict:
     offs = np.zeros(nr.value + 1, dtype=np.int64)
     mem = np.zeros(max(nm.value, 1), dtype=np.int32)
     _check(L.fbn_export_sepsets(h.ptr, C.byref(nr), C.byref(nm), _ptr(pairs), _ptr(offs), _ptr(mem)), h)
+    if not as_dict:
+        return pairs[: nr.value], offs, mem[: nm.value]
     return {(int(pairs[k, 0]), int(pairs[k, 1])): tuple(int(v) for v in mem[offs[k]:offs[k + 1]])
             for k in range(nr.value)}
 
@@ -247,7 +262,8 @@ def fbn_get_stats(h: Handle) -> dict:
     d = s.depths
     return {"depths": d, "launches": int(s.launches), "edges": list(s.edges[:d]),
             "tests": list(s.tests[:d]), "tests_oracle": list(s.tests_oracle[:d]),
-            "removed": list(s.removed[:d]), "ms": list(s.ms[:d]), "test_ms": list(s.test_ms[:d])}
+            "removed": list(s.removed[:d]), "ms": list(s.ms[:d]), "test_ms": list(s.test_ms[:d]),
+            "gram_ms": float(s.gram_ms), "gram_rows": int(s.gram_rows), "gram_samples": int(s.gram_samples)}
 
 
 def fbn_last_error(h: Handle | None = None) -> str:

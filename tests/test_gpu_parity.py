@@ -193,3 +193,22 @@ def test_errors(F):
     with pytest.raises(F.FbnError) as e:
         F.fbn_ci_test(hb, 0, 1, [2, 3])
     assert e.value.code == -5
+
+
+def test_update_data(F):
+    a_data, a_ar, alpha, md, _ = bnsynth.workload("small")
+    rng = np.random.default_rng(77)
+    b_data = np.stack([rng.integers(0, r, a_data.shape[1]) for r in a_ar]).astype(np.uint8)
+    h = F.fbn_create(a_data, a_ar)
+    F.fbn_learn_skeleton(h, alpha, md)
+    F.fbn_update_data(h, b_data)
+    adj = F.fbn_learn_skeleton(h, alpha, md)
+    ref = oracle.pc_stable(b_data, a_ar, alpha, md)
+    hard, _, _ = compare(adj, F.fbn_export_sepsets(h), ref)
+    assert not hard
+    assert F.fbn_ci_test(h, 0, 1, [2])[0] == pytest.approx(oracle.ci_test(b_data, a_ar, 0, 1, [2])[0], rel=1e-6)
+    bad = b_data.copy()
+    bad[3, 11] = a_ar[3]
+    with pytest.raises(F.FbnError) as e:
+        F.fbn_update_data(h, bad)
+    assert e.value.code == -2
