@@ -92,7 +92,12 @@ struct Workspace {
     double* crit_vals = nullptr;
     double crit_alpha = -1.0;
     cudaEvent_t ev[FBN_MAX_DEPTHS + 1] = {};
-    cudaEvent_t kev[4] = {};
+    cudaEvent_t kev[2 * FBN_MAX_DEPTHS + 2] = {};   // test kernels of each depth; the Gram
+    cudaEvent_t done[FBN_MAX_DEPTHS] = {};          // loop flag of each depth copied to the host
+    DepthRecord* d_rec = nullptr;
+    DepthRecord* h_rec = nullptr;                   // pinned
+    int* h_active = nullptr;                        // pinned, one flag per depth
+    long long gs_cells = 0;                         // cells per group of the global scratch
     bool events = false;
 
     void release()
@@ -106,7 +111,11 @@ struct Workspace {
         if (events) {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
+            for (auto& e : done) cudaEventDestroy(e);
         }
+        dfree(d_rec);
+        if (h_rec) cudaFreeHost(h_rec);
+        if (h_active) cudaFreeHost(h_active);
         *this = Workspace();
     }
 };
@@ -191,6 +200,8 @@ bool is_device_ptr(const void* p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+int ensure_order(fbn_handle* h, Workspace& ws, long long maxc);
+
 int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, int nprob, int total_vtx)
 {
     if (!ws.d_ctr) {
@@ -198,7 +209,13 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         CK(cudaMallocHost((void**)&ws.h_ctr, sizeof(DepthCounters)));
         for (auto& e : ws.ev) CK(cudaEventCreate(&e));
         for (auto& e : ws.kev) CK(cudaEventCreate(&e));
+        for (auto& e : ws.done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ws.events = true;
+        CK(dalloc(&ws.d_rec, kMaxDepthRecords));
+        CK(cudaMallocHost((void**)&ws.h_rec, kMaxDepthRecords * sizeof(DepthRecord)));
+        CK(cudaMallocHost((void**)&ws.h_active, kMaxDepthRecords * sizeof(int)));
+        const int orc = ensure_order(h, ws, kMaxPasses);
+        if (orc) return orc;
         CK(dalloc(&ws.crit_keys, kCritCap));
         CK(dalloc(&ws.crit_vals, kCritCap));
     }
@@ -252,11 +269,11 @@ int ensure_order(fbn_handle* h, Workspace& ws, long long maxc)
     dfree(ws.hist); dfree(ws.alive); dfree(ws.base); dfree(ws.cursor);
     ws.hist = ws.alive = ws.base = ws.cursor = nullptr;
     ws.ord_cap = 0;
-    const long long cap = std::max(maxc + 1, 1024LL);
-    CK(dalloc(&ws.hist, cap));
-    CK(dalloc(&ws.alive, cap));
-    CK(dalloc(&ws.base, cap));
-    CK(dalloc(&ws.cursor, cap));
+    const long long cap = maxc + 1;   // per class; both classes side by side
+    CK(dalloc(&ws.hist, 2 * cap));
+    CK(dalloc(&ws.alive, 2 * cap));
+    CK(dalloc(&ws.base, 2 * cap));
+    CK(dalloc(&ws.cursor, 2 * cap));
     ws.ord_cap = cap;
     return FBN_OK;
 }
@@ -308,6 +325,7 @@ int check_status(fbn_handle* h, unsigned status)
     if (status & kStatusSepPool) return fail(h, FBN_ECUDA, "separating-set pool overflow");
     if (status & kStatusEdges) return fail(h, FBN_ECUDA, "edge list overflow");
     if (status & kStatusTimeout) return fail(h, FBN_ETIMEOUT, "a bounded device wait gave up");
+    if (status & kStatusScratch) return fail(h, FBN_ENOMEM, "global table scratch too small");
     return FBN_OK;
 }
 
@@ -382,12 +400,18 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
     return FBN_OK;
 }
 
-// The depth loop of Algorithm 1 over one or more problems sharing a stream.
-int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+// The depth loop of Algorithm 1 over one or more problems sharing a stream,
+// one attempt.  Every kernel of a depth takes the depth and the sizes from the
+// device counters, so the host queues depth d+1 before depth d has finished
+// and only waits for the loop flag of depth d-1.  *retry is set when a
+// separating-set pool or global-table scratch turned out too small (both are
+// grown before returning).
+int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, bool* retry)
 {
     fbn_handle* h = hs[0];
     Workspace& ws = h->ws;
     cudaStream_t st = h->stream;
+    *retry = false;
     CK(cudaSetDevice(h->device));
     long long edge_cap = 0;
     int max_n = 0, total_vtx = 0;
@@ -407,6 +431,10 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
     }
     int rc = grow_workspace(h, ws, edge_cap, max_n, k, total_vtx);
     if (rc) return rc;
+    if (ws.sep_cap == 0) {
+        rc = ensure_sep_pool(h, ws, 2 * edge_cap + 1024, 0, st);
+        if (rc) return rc;
+    }
     CK(cudaMemcpyAsync(ws.probs, P.data(), k * sizeof(ProblemDev), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ws.vtx_prob, vtx_prob.data(), total_vtx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ws.vtx_first, vtx_first.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -417,173 +445,161 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
     int dev_sms = 0;
     CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
     CK(set_kernel_smem(kSmemBytes));
-    // CTAs per SM of each group size on the small-table configuration, and of
-    // CTA groups on the big-table one
-    const int gsizes[4] = {32, 64, 128, kTestThreads};
-    int grid_small[4];
-    for (int k = 0; k < 4; ++k) grid_small[k] = dev_sms * std::max(1, pool_blocks_per_sm(gsizes[k], kWarpSmemBytes));
-    const int grid_big = dev_sms * std::max(1, pool_blocks_per_sm(kTestThreads, kSmemBytes));
+    // CTAs of the small-table pool (any group size) and of the big-table pool
+    const int grid_small = dev_sms * std::max(1, pool_blocks_per_sm(kClassWarp, kWarpSmemBytes));
+    const int grid_big = dev_sms * std::max(1, pool_blocks_per_sm(kClassCta, kSmemBytes));
+    const long long groups[3] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2};
+    int max_ar = 2;
+    for (int p = 0; p < k; ++p) max_ar = std::max(max_ar, hs[p]->max_arity);
+    const int grid_aux = dev_sms * 4;   // grid-stride helpers (ordering, removal)
     const int gs = h->opt.group_size > 0 ? h->opt.group_size : kDefaultGs;
     const bool plain = h->opt.form == FBN_FORM_PLAIN;
     const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
     const bool gram = !plain && use_gram(h, k);
+    const int forced = h->opt.group_threads;
     if (ws.crit_alpha != alpha) {
         CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
         ws.crit_alpha = alpha;
     }
+    CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, 0};
+
+    CK(cudaMemsetAsync(ws.d_rec, 0, kMaxDepthRecords * sizeof(DepthRecord), st));
+    CK(cudaMemsetAsync(ws.hist, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ws.cursor, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
+    DepthCounters c0{};
+    c0.active = 1;
+    *ws.h_ctr = c0;
+    CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
+
+    PoolArgs base{};
+    base.probs = ws.probs;
+    base.edges = ws.edges;
+    base.min_accept = ws.min_accept;
+    base.edge_cap = ws.edge_cap;
+    base.sorted = ws.sorted;
+    base.ctr = ws.d_ctr;
+    base.binom = ws.binom;
+    base.binom_rows = ws.brows;
+    base.crit = ct;
+    base.gs = plain ? 1 : gs;
+    base.alpha = alpha;
+
+    int queued = 0;
+    for (int d = 0; d < kMaxDepthRecords; ++d) {
+        if (max_depth >= 0 && d > max_depth) break;
+        CK(cudaEventRecord(ws.ev[d], st));
+        launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
+        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, base.gs, ws.binom, ws.brows, wcap, ws.edges,
+                     ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
+        launches += 2;
+        // the big-table class can only be non-empty once max_arity^(d+2) tops
+        // the small-table bound
+        long long bound = 1;
+        for (int q = 0; q < d + 2 && bound <= wcap; ++q) bound *= max_ar;
+        const bool big_possible = bound > wcap;
+        CK(cudaEventRecord(ws.kev[2 * d], st));
+        if (d == 0 && gram) {
+            rc = run_gram(h, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS], ws.kev[2 * FBN_MAX_DEPTHS + 1]);
+            if (rc) return rc;
+            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, h->d_G, h->Mp, h->d_off, ws.min_accept, ct, alpha,
+                                   ws.d_ctr, grid_aux, st));
+            launches += 3;
+        } else {
+            for (int cls = 0; cls < 2; ++cls) {
+                if (cls == kClassCta && !big_possible) continue;
+                PoolArgs a = base;
+                a.cls = cls;
+                const bool small = cls == kClassWarp && !plain;
+                const size_t smem = small ? kWarpSmemBytes : kSmemBytes;
+                a.smem_ints = (int)(smem / 4);
+                if (!small && ws.gs_cells > 0) {
+                    a.gscratch = ws.gscratch;
+                    a.gscratch_ints = 3 * ws.gs_cells + 64;
+                }
+                if (plain) {
+                    launch_plain(a, grid_big, kSmemBytes, st);
+                    launches += 1;
+                    continue;
+                }
+                unsigned long long* cls_base = ws.base + cls * ws.ord_cap;
+                a.base = cls_base;
+                a.sorted = ws.sorted;
+                launch_order(ws.edges, ws.edge_cap, cls, base.gs, ws.d_ctr, ws.hist + cls * ws.ord_cap,
+                             ws.alive + cls * ws.ord_cap, cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups,
+                             forced, grid_aux, st);
+                launches += 2;
+                launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
+                launches += 1;
+                // the two classes share the sorted array: the next class's ordering
+                // runs after this pool on the same stream
+            }
+        }
+        CK(cudaGetLastError());
+        CK(cudaEventRecord(ws.kev[2 * d + 1], st));
+        launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
+                     grid_aux, st);
+        launch_depth_end(ws.d_ctr, ws.d_rec, max_depth, ws.hist, ws.cursor, st);
+        launches += 2;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&ws.h_active[d], &ws.d_ctr->active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(ws.done[d], st));
+        queued = d + 1;
+        // depth d is queued; stop queueing once depth d-1 ended the loop
+        if (d >= 1) {
+            CK(cudaEventSynchronize(ws.done[d - 1]));
+            if (!ws.h_active[d - 1]) break;
+        }
+    }
+    CK(cudaEventRecord(ws.ev[queued], st));
+    CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ws.h_rec, ws.d_rec, kMaxDepthRecords * sizeof(DepthRecord), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const DepthCounters& c = *ws.h_ctr;
+    if (c.status & (kStatusSepPool | kStatusScratch)) {
+        if (c.status & kStatusSepPool) {
+            rc = ensure_sep_pool(h, ws, 2 * ws.sep_cap + 2 * (long long)c.sep_used, 0, st);
+            if (rc) return rc;
+        }
+        if (c.status & kStatusScratch) {
+            if (c.need_cells <= 0 || c.need_cells > kMaxCells) return check_status(h, kStatusTooBig);
+            ws.gs_cells = std::max<long long>(2 * ws.gs_cells, c.need_cells);
+            rc = ensure_gscratch(h, ws, (3 * ws.gs_cells + 64) * grid_big);
+            if (rc) return rc;
+        }
+        *retry = true;
+        return FBN_OK;
+    }
+    rc = check_status(h, c.status);
+    if (rc) return rc;
 
     fbn_stats stats{};
-    unsigned long long sep_used = 0;
-    for (int d = 0;; ++d) {
-        if (max_depth >= 0 && d > max_depth) break;
-        if (d > kMaxD) return fail(h, FBN_ETOOBIG, "depth %d exceeds the supported %d", d, kMaxD);
-        if (d >= FBN_MAX_DEPTHS) return fail(h, FBN_ETOOBIG, "depth %d exceeds FBN_MAX_DEPTHS", d);
-        DepthCounters c0{};
-        c0.sep_used = sep_used;
-        *ws.h_ctr = c0;
-        CK(cudaEventRecord(ws.ev[d], st));
-        CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
-        launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st);
-        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, d, plain ? 1 : gs, ws.binom, ws.brows, wcap,
-                     ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, st);
-        CK(cudaGetLastError());
-        launches += 2;
-        CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        rc = check_status(h, ws.h_ctr->status);
-        if (rc) return rc;
-        const long long Ec[2] = {(long long)ws.h_ctr->n_edges[0], (long long)ws.h_ctr->n_edges[1]};
-        const long long E = Ec[0] + Ec[1];
-        if (E == 0) break;   // no edge has a side with >= d candidates: Algorithm 1 stops
-        const long long maxc[2] = {(long long)ws.h_ctr->maxc[0], (long long)ws.h_ctr->maxc[1]};
-        const long long mcells[2] = {(long long)ws.h_ctr->max_cells[0], (long long)ws.h_ctr->max_cells[1]};
-        if (mcells[1] > kMaxCells)
-            return fail(h, FBN_ETOOBIG, "depth %d may need tables of more than %lld cells", d, kMaxCells);
-        rc = ensure_sep_pool(h, ws, (long long)sep_used + E * d + 1, (long long)sep_used, st);
-        if (rc) return rc;
-
-        CK(cudaEventRecord(ws.kev[0], st));
-        int group_used[2] = {0, 0};
-        const bool gram0 = d == 0 && gram;
-        if (gram0) {
-            rc = run_gram(h, &ws.d_ctr->status, ws.kev[2], ws.kev[3]);
-            if (rc) return rc;
-            CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, 0};
-            for (int cls = 0; cls < 2; ++cls) {
-                if (Ec[cls] == 0) continue;
-                const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
-                CK(launch_pairs_decide(ws.edges + off, Ec[cls], ws.probs, h->d_G, h->Mp, h->d_off,
-                                       ws.min_accept + off, ct, alpha, &ws.d_ctr->tests, &ws.d_ctr->status, st));
-            }
-            launches += 5;
-        }
-        for (int cls = 0; cls < 2 && !gram0; ++cls) {
-            if (Ec[cls] == 0) continue;
-            const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
-            PoolArgs a{};
-            a.probs = ws.probs;
-            a.edges = ws.edges + off;
-            a.min_accept = ws.min_accept + off;
-            a.sorted = ws.sorted;
-            a.next_item = &ws.d_ctr->next_item[cls];
-            a.total_items = &ws.d_ctr->total_items[cls];
-            a.tests = &ws.d_ctr->tests;
-            a.status = &ws.d_ctr->status;
-            a.binom = ws.binom;
-            a.binom_rows = ws.brows;
-            a.crit.keys = ws.crit_keys;
-            a.crit.vals = ws.crit_vals;
-            a.crit.cap = kCritCap;
-            a.maxc = maxc[cls];
-            a.d = d;
-            a.gs = plain ? 1 : gs;
-            a.alpha = alpha;
-            const bool warp_cls = cls == kClassWarp && !plain;
-            const size_t smem = warp_cls ? kWarpSmemBytes : kSmemBytes;
-            a.smem_ints = (int)(smem / 4);
-            // group size: the smallest whose group count the edges still fill
-            // twice over (more groups hide latency; bigger groups finish a test
-            // sooner when there are few of them)
-            int group = kTestThreads, grid = grid_big;
-            if (warp_cls) {
-                group = kTestThreads;
-                grid = grid_small[3];
-                for (int k = 0; k < 3; ++k) {
-                    const long long groups = (long long)grid_small[k] * (kTestThreads / gsizes[k]);
-                    if (Ec[cls] >= 2 * groups) {
-                        group = gsizes[k];
-                        grid = grid_small[k];
-                        break;
-                    }
-                }
-            }
-            if (warp_cls && h->opt.group_threads) {
-                group = h->opt.group_threads;
-                for (int k = 0; k < 4; ++k)
-                    if (gsizes[k] == group) grid = grid_small[k];
-            }
-            if (plain) grid = (int)std::min<long long>(Ec[cls], fits_smem(mcells[cls]) ? (1LL << 30) : grid_big);
-            group_used[cls] = group;
-            if (!warp_cls && !fits_smem(mcells[cls])) {
-                a.gscratch_ints = 3 * mcells[cls] + 64;
-                rc = ensure_gscratch(h, ws, a.gscratch_ints * grid);
-                if (rc) return rc;
-                a.gscratch = ws.gscratch;
-            }
-            if (plain) {
-                launch_plain(a, Ec[cls], grid, kSmemBytes, st);
-                launches += 1;
-            } else {
-                rc = ensure_order(h, ws, maxc[cls]);
-                if (rc) return rc;
-                a.base = ws.base;
-                launch_order(a.edges, Ec[cls], gs, maxc[cls], ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted,
-                             &ws.d_ctr->total_items[cls], &ws.d_ctr->next_item[cls], st);
-                launch_pool(a, group, grid, smem, st);
-                launches += 4;
-            }
-            CK(cudaGetLastError());
-        }
-        CK(cudaEventRecord(ws.kev[1], st));
-        for (int cls = 0; cls < 2; ++cls) {
-            if (Ec[cls] == 0) continue;
-            const long long off = cls == kClassWarp ? 0 : ws.edge_cap - Ec[1];
-            launch_apply(ws.probs, ws.edges + off, ws.min_accept + off, Ec[cls], d, ws.binom, ws.sep_pool,
-                         ws.sep_cap, ws.d_ctr, st);
-            launches += 1;
-        }
-        CK(cudaGetLastError());
-        CK(cudaEventRecord(ws.ev[d + 1], st));
-        CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        rc = check_status(h, ws.h_ctr->status);
-        if (rc) return rc;
+    for (int d = 0; d < queued; ++d) {
+        const DepthRecord& r = ws.h_rec[d];
+        if (r.edges == 0) break;   // the depth that found no edge: Algorithm 1 stopped before it
+        stats.depths = d + 1;
+        stats.edges[d] = r.edges;
+        stats.tests[d] = r.tests;
+        stats.tests_oracle[d] = r.tests_oracle;
+        stats.removed[d] = r.removed;
         float ms = 0.f, kms = 0.f;
         CK(cudaEventElapsedTime(&ms, ws.ev[d], ws.ev[d + 1]));
-        CK(cudaEventElapsedTime(&kms, ws.kev[0], ws.kev[1]));
-        stats.test_ms[d] = kms;
-        if (gram0) {
-            float gms = 0.f;
-            CK(cudaEventElapsedTime(&gms, ws.kev[2], ws.kev[3]));
-            stats.gram_ms = gms;
-            stats.gram_rows = h->M;
-            stats.gram_samples = h->K;
-        }
-        stats.depths = d + 1;
-        stats.edges[d] = E;
-        stats.tests[d] = (int64_t)ws.h_ctr->tests;
-        stats.tests_oracle[d] = (int64_t)ws.h_ctr->tests_oracle;
-        stats.removed[d] = (int64_t)ws.h_ctr->removed;
+        CK(cudaEventElapsedTime(&kms, ws.kev[2 * d], ws.kev[2 * d + 1]));
         stats.ms[d] = ms;
-        sep_used = ws.h_ctr->sep_used;
+        stats.test_ms[d] = kms;
     }
-
+    if (gram && queued > 0) {
+        float gms = 0.f;
+        CK(cudaEventElapsedTime(&gms, ws.kev[2 * FBN_MAX_DEPTHS], ws.kev[2 * FBN_MAX_DEPTHS + 1]));
+        stats.gram_ms = gms;
+        stats.gram_rows = h->M;
+        stats.gram_samples = h->K;
+    }
     stats.launches = launches;
     for (int p = 0; p < k; ++p) {
         hs[p]->stats = stats;
         hs[p]->learnt = true;
         hs[p]->sep_pending = true;
-        hs[p]->sep_pool_used = sep_used;
+        hs[p]->sep_pool_used = c.sep_used;
     }
     if (k == 1) return FBN_OK;   // a single problem's sets stay on the device until asked for
     // a batch shares the first handle's pool: bring every problem's sets over now
@@ -592,6 +608,16 @@ int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
         if (rc) return rc;
     }
     return FBN_OK;
+}
+
+int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+{
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        bool retry = false;
+        const int rc = run_skeleton_once(hs, k, alpha, max_depth, &retry);
+        if (rc || !retry) return rc;
+    }
+    return fail(hs[0], FBN_ENOMEM, "scratch or separating-set pool kept overflowing");
 }
 
 int copy_adj(fbn_handle* h, uint8_t* adj_out)

@@ -356,14 +356,12 @@ __global__ void k_onehot(const uint8_t* __restrict__ data, long long ld, int n, 
     }
 }
 
-// Depth-0 decisions from the Gram: one thread per edge (i<j) of the list.
-__global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long E, const ProblemDev* __restrict__ probs,
-                               const int32_t* __restrict__ G, int Mp, const int32_t* __restrict__ off,
-                               unsigned long long* __restrict__ min_accept, CritTableDev crit, double alpha,
-                               unsigned long long* tests, unsigned* status)
+__device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, long long e,
+                                            const ProblemDev* __restrict__ probs, const int32_t* __restrict__ G,
+                                            int Mp, const int32_t* __restrict__ off,
+                                            unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
+                                            double alpha, DepthCounters* ctr)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
     const EdgeWork w = edges[e];
     const ProblemDev& P = probs[w.prob];
     const int rx = P.ar[w.i], ry = P.ar[w.j];
@@ -382,7 +380,7 @@ __global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long E, 
     // terms with FP32 logs summed in FP64 (each term within 3.2e-7 of its
     // magnitude); exact FP64 only when crit lies inside the error band
     const long long df = (long long)(rx - 1) * (ry - 1);
-    const double c = crit_get(crit, df, alpha, status);
+    const double c = crit_get(crit, df, alpha, &ctr->status);
     double acc = 0.0, mag = 0.0;
     for (int x = 0; x < rx; ++x)
         for (int y = 0; y < ry; ++y) {
@@ -414,9 +412,23 @@ __global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long E, 
         accept = 2.0 * ex < c;
     }
     if (accept) min_accept[e] = 0;
-    atomicAdd(tests, 1ULL);
+    atomicAdd(&ctr->tests, 1ULL);
 }
 
+
+// Depth-0 decisions from the Gram: one thread per edge (i<j) of both classes
+// of the edge list (class 0 at the front of the array, class 1 at the back).
+__global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long edge_cap,
+                               const ProblemDev* __restrict__ probs, const int32_t* __restrict__ G, int Mp,
+                               const int32_t* __restrict__ off, unsigned long long* __restrict__ min_accept,
+                               CritTableDev crit, double alpha, DepthCounters* ctr)
+{
+    if (!ctr->active) return;
+    const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
+         k += (long long)gridDim.x * blockDim.x)
+        pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, G, Mp, off, min_accept, crit, alpha, ctr);
+}
 // Mirror the upper block triangle into the lower one (row < col -> col, row).
 __global__ void k_symmetrize(int32_t* G, int Mp, int M)
 {
@@ -489,13 +501,11 @@ cudaError_t launch_gram(const uint8_t* E, int Mp, long long K, int32_t* G, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_pairs_decide(const EdgeWork* edges, long long E, const ProblemDev* probs, const int32_t* G,
+cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs, const int32_t* G,
                                 int Mp, const int32_t* off, unsigned long long* min_accept, const CritTableDev& crit,
-                                double alpha, unsigned long long* tests, unsigned* status, cudaStream_t st)
+                                double alpha, DepthCounters* ctr, int grid, cudaStream_t st)
 {
-    if (E == 0) return cudaSuccess;
-    k_pairs_decide<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(edges, E, probs, G, Mp, off, min_accept, crit, alpha,
-                                                                tests, status);
+    k_pairs_decide<<<grid, 256, 0, st>>>(edges, edge_cap, probs, G, Mp, off, min_accept, crit, alpha, ctr);
     return cudaGetLastError();
 }
 

@@ -22,6 +22,7 @@ constexpr unsigned kStatusNumeric = 2u;   // p-value iteration hit its cap
 constexpr unsigned kStatusSepPool = 4u;   // separating-set pool overflow
 constexpr unsigned kStatusEdges = 8u;     // edge list overflow
 constexpr unsigned kStatusTimeout = 16u;  // a bounded device wait gave up
+constexpr unsigned kStatusScratch = 32u;  // a table needed more global scratch than allocated
 constexpr int kMaxArityPairs = 256;       // arity bound of the depth-0 pair epilogue
 
 // One learning problem (one data set).  Arrays are device pointers.
@@ -55,6 +56,8 @@ struct EdgeWork {
 constexpr int kClassWarp = 0;
 constexpr int kClassCta = 1;
 
+// Device-side state of the depth loop.  Per-depth fields are cleared by
+// k_depth_begin; d, active, status and sep_used persist across depths.
 struct DepthCounters {
     unsigned long long n_edges[2];      // edges per class
     unsigned long long maxc[2];         // largest chunk count per class
@@ -63,11 +66,37 @@ struct DepthCounters {
     unsigned long long tests;           // CI tests executed
     unsigned long long tests_oracle;    // tests of the sequential order (gs = 1)
     unsigned long long removed;         // edges removed
-    unsigned long long sep_used;        // separating-set pool entries in use
     unsigned long long max_cells[2];    // upper bound of table cells per class
-    unsigned int status;
-    unsigned int pad[3];
+    unsigned long long sep_used;        // separating-set pool entries in use (persists)
+    unsigned int status;                // error bits (persists)
+    int d;                              // current depth (persists)
+    int active;                         // 1 while Algorithm 1 continues (persists)
+    int gsel;                           // group size of the small-table class this depth
+    int need_cells;                     // largest table that missed the global scratch (persists)
+    int pad;
 };
+
+// Per-depth record written by k_depth_end.
+constexpr int kMaxDepthRecords = 64;
+struct DepthRecord {
+    long long edges, tests, tests_oracle, removed;
+};
+
+// Passes of the work pool are capped: an edge with more ranks than
+// kMaxPasses * gs takes chunks of ceil(total / kMaxPasses) ranks.
+constexpr long long kMaxPasses = 4096;
+
+__host__ __device__ __forceinline__ long long chunk_ranks(long long total, int gs)
+{
+    const long long c = (total + kMaxPasses - 1) / kMaxPasses;
+    return c > gs ? c : gs;
+}
+
+__host__ __device__ __forceinline__ long long chunk_count(long long total, int gs)
+{
+    const long long c = chunk_ranks(total, gs);
+    return (total + c - 1) / c;
+}
 
 // Cache of critical values, see fbn_device.cuh.
 struct CritTableDev {
@@ -77,23 +106,21 @@ struct CritTableDev {
     int pad;
 };
 
-// Work pool of one depth and one edge class.
+// Work pool of one depth and one edge class.  Sizes, the depth and the class
+// sub-array come from the DepthCounters on the device.
 struct PoolArgs {
     const ProblemDev* probs;
-    const EdgeWork* edges;            // class sub-array
-    unsigned long long* min_accept;   // class sub-array, lowest accepting rank, init = total
+    const EdgeWork* edges;            // whole edge array (class 0 from the front, class 1 from the back)
+    unsigned long long* min_accept;   // per edge, lowest accepting rank, init = total
+    long long edge_cap;
     const int32_t* sorted;            // class edges by chunk count, descending
     const unsigned long long* base;   // [maxc + 1] first item of pass k
-    unsigned long long* next_item;
-    const unsigned long long* total_items;
-    unsigned long long* tests;
-    unsigned* status;
+    DepthCounters* ctr;
     const long long* binom;           // [binom_rows][kBinomCols]
     int* gscratch;                    // global tables, gscratch_ints per group
     long long gscratch_ints;
     CritTableDev crit;
-    long long maxc;
-    int32_t d;
+    int32_t cls;
     int32_t gs;
     int32_t smem_ints;
     int32_t binom_rows;

@@ -6,9 +6,9 @@
 //   k_edges      edges i<j with at least one test, with their rank space
 //                |X-side| + |Y-side|, split into a warp class (tables that fit
 //                a warp's share of shared memory) and a CTA class
-//   k_chunk_hist / k_scan / k_place
-//                order each class by chunk count, so that pass k of the work
-//                pool is a prefix of that order
+//   k_scan / k_place
+//                order each class by chunk count (counted by k_edges), so that
+//                pass k of the work pool is a prefix of that order
 //   k_pool<G>    persistent CI-level work pool (Section IV-B): each group (a
 //                warp or a CTA) claims work items -- one chunk of gs
 //                consecutive conditioning sets of one edge -- from one atomic
@@ -19,6 +19,11 @@
 //                conditioning sets with early exit
 //   k_apply      end-of-depth removal over the snapshot; the separating set is
 //                the conditioning set of the lowest accepting rank
+//   k_depth_end  records the depth, decides whether Algorithm 1 goes on and
+//                clears the per-depth counters for the next depth
+// Every kernel reads the depth and the sizes from the device counters, so the
+// host can queue depth d+1 before depth d has finished; a depth queued after
+// the loop ended finds active == 0 and does nothing.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -29,11 +34,11 @@ namespace fbn {
 
 // --------------------------------------------------------------------------
 __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
-                           const int32_t* __restrict__ vtx_first, int total_vertices)
+                           const int32_t* __restrict__ vtx_first, int total_vertices, const DepthCounters* ctr)
 {
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (g >= total_vertices) return;
+    if (g >= total_vertices || !ctr->active) return;
     const int p = vtx_prob[g];
     const ProblemDev P = probs[p];
     const int v = g - vtx_first[p];
@@ -59,14 +64,15 @@ __device__ __forceinline__ long long binom_sat(const long long* B, int brows, in
 }
 
 __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
-                        const int32_t* __restrict__ vtx_first, int total_vertices, int d, int gs,
+                        const int32_t* __restrict__ vtx_first, int total_vertices, int gs,
                         const long long* __restrict__ binom, int brows, long long warp_cells_cap,
                         EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
-                        long long edge_cap, DepthCounters* ctr)
+                        long long edge_cap, DepthCounters* ctr, unsigned long long* __restrict__ hist)
 {
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
-    if (g >= total_vertices) return;
+    if (g >= total_vertices || !ctr->active) return;
+    const int d = ctr->d;
     const int p = vtx_prob[g];
     const ProblemDev P = probs[p];
     const int i = g - vtx_first[p];
@@ -123,7 +129,8 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
             w.cnt_i = cnt_i; w.total = total;
             edges[e] = w;
             min_accept[e] = (unsigned long long)total;
-            const unsigned long long ch = (unsigned long long)((total + gs - 1) / gs);
+            const unsigned long long ch = (unsigned long long)chunk_count(total, gs);
+            atomicAdd(&hist[c * (kMaxPasses + 1) + ch], 1ULL);   // chunk-count histogram of the class
             mc[c] = ch > mc[c] ? ch : mc[c];
             mcell[c] = cells > mcell[c] ? cells : mcell[c];
         }
@@ -145,13 +152,11 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
 }
 
 // --------------------------------------------------------------------------
-__global__ void k_chunk_hist(const EdgeWork* __restrict__ edges, long long E, int gs,
-                             unsigned long long* __restrict__ hist)
+// Edges of class cls: class 0 fills the edge array from the front, class 1
+// from the back.
+__device__ __forceinline__ long long class_base(const DepthCounters* ctr, int cls, long long edge_cap)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const long long ch = (edges[e].total + gs - 1) / gs;
-    atomicAdd(&hist[ch], 1ULL);
+    return cls == 0 ? 0 : edge_cap - (long long)ctr->n_edges[1];
 }
 
 // One CTA: alive[k] = #edges with more than k chunks (k = 0..maxc), base[k] =
@@ -184,11 +189,25 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
     return before + x - v;
 }
 
-__global__ void k_scan(const unsigned long long* __restrict__ hist, long long maxc,
+// One CTA per class.  Also picks the group size of the small-table class:
+// the smallest whose group count the edges still fill twice over (groups[k]
+// = groups available with size 32 << k), unless the caller forces one.
+__global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, DepthCounters* ctr,
                        unsigned long long* __restrict__ alive, unsigned long long* __restrict__ base,
-                       unsigned long long* total_items, unsigned long long* next_item)
+                       long long g32, long long g64, long long g128, int forced_group)
 {
     __shared__ unsigned long long sh[32];
+    if (!ctr->active) return;
+    const long long maxc = (long long)ctr->maxc[cls];
+    if (threadIdx.x == 0 && cls == 0) {
+        const long long E = (long long)ctr->n_edges[0];
+        int g = kTestThreads;
+        if (E >= 2 * g128) g = 128;
+        if (E >= 2 * g64) g = 64;
+        if (E >= 2 * g32) g = 32;
+        ctr->gsel = forced_group ? forced_group : g;
+    }
+    if (ctr->n_edges[cls] == 0) return;
     const int T = blockDim.x;
     const long long len = maxc + 1;
     const long long seg = (len + T - 1) / T;
@@ -216,20 +235,23 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, long long ma
         run += alive[c];
     }
     if (fhi == len && flo < fhi) {
-        *total_items = base[maxc];
-        *next_item = 0;
+        ctr->total_items[cls] = base[maxc];
+        ctr->next_item[cls] = 0;
     }
 }
 
-__global__ void k_place(const EdgeWork* __restrict__ edges, long long E, int gs,
-                        const unsigned long long* __restrict__ alive, unsigned long long* __restrict__ cursor,
-                        int32_t* __restrict__ sorted)
+__global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, int cls, int gs,
+                        const DepthCounters* ctr, const unsigned long long* __restrict__ alive,
+                        unsigned long long* __restrict__ cursor, int32_t* __restrict__ sorted)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const long long ch = (edges[e].total + gs - 1) / gs;
-    const unsigned long long pos = alive[ch] + atomicAdd(&cursor[ch], 1ULL);
-    sorted[pos] = (int32_t)e;
+    if (!ctr->active) return;
+    const long long E = (long long)ctr->n_edges[cls];
+    const EdgeWork* ed = edges + class_base(ctr, cls, edge_cap);
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+        const long long ch = chunk_count(ed[e].total, gs);
+        const unsigned long long pos = alive[ch] + atomicAdd(&cursor[ch], 1ULL);
+        sorted[pos] = (int32_t)e;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -292,99 +314,143 @@ __device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& 
 
 // Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
 template <int G>
-__device__ __forceinline__ int run_rank(const PoolArgs& a, const ProblemDev& P, const EdgeWork& w, long long rk,
+__device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w, long long rk,
                                         bool fresh, GroupState& S, TestSpec& spec, int* slice, long long slice_ints,
                                         int* gtab, double* red)
 {
-    if (!setup_rank<G>(P, w, a.d, rk, fresh, S, a.binom, spec, a.status)) return -1;
+    unsigned* status = &a.ctr->status;
+    if (!setup_rank<G>(P, w, d, rk, fresh, S, a.binom, spec, status)) return -1;
     int* M = nullptr;
     const int* T = grp_table<G>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
-    if (!T) {
-        if (Grp<G>::rank() == 0) atomicOr(a.status, kStatusTooBig);
+    if (!T) {   // the global scratch is too small: the host grows it and starts over
+        if (Grp<G>::rank() == 0) {
+            atomicOr(status, kStatusScratch);
+            atomicMax(&a.ctr->need_cells, (int)spec.cells);
+        }
         return -1;
     }
     grp_marginals<G>(spec, T, M);
     if (Grp<G>::rank() == 0) {
         const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
-        S.crit = crit_get(a.crit, df, a.alpha, a.status);
-        atomicAdd(a.tests, 1ULL);
+        S.crit = crit_get(a.crit, df, a.alpha, status);
+        atomicAdd(&a.ctr->tests, 1ULL);
     }
     Grp<G>::sync();
     return grp_decide<G>(spec, T, M, S.crit, red) ? 1 : 0;
 }
 
+// Shared state of a pool CTA, sized for the most groups per CTA (8 warps).
+struct PoolShared {
+    TestSpec spec[kTestThreads / 32];
+    GroupState st[kTestThreads / 32];
+    double red[32];
+    unsigned long long base[kBaseSmem];
+};
+
 template <int G>
-__global__ void __launch_bounds__(kTestThreads, G == kTestThreads ? 2 : 3) k_pool(PoolArgs a)
+__device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShared& sh)
 {
-    extern __shared__ int smem[];
     constexpr int NG = kTestThreads / G;   // groups per CTA
-    __shared__ TestSpec spec_s[NG];
-    __shared__ GroupState st_s[NG];
-    __shared__ double red[32];
-    __shared__ unsigned long long base_s[kBaseSmem];
+    const DepthCounters* ctr = a.ctr;
+    const int d = ctr->d;
+    const long long maxc = (long long)ctr->maxc[a.cls];
+    const unsigned long long total = ctr->total_items[a.cls];
+    if (total == 0) return;
+    const long long cb = class_base(ctr, a.cls, a.edge_cap);
+    const EdgeWork* edges = a.edges + cb;
+    unsigned long long* min_accept = a.min_accept + cb;
+    unsigned long long* next_item = &a.ctr->next_item[a.cls];
     const int g = Grp<G>::gid();
     const int r = Grp<G>::rank();
     const long long slice_ints = a.smem_ints / NG;
     int* slice = smem + g * slice_ints;
     int* gtab = a.gscratch ? a.gscratch + ((long long)blockIdx.x * NG + g) * a.gscratch_ints : nullptr;
-    const unsigned long long total = *a.total_items;
-    const bool base_in_smem = a.maxc + 1 <= kBaseSmem;
+    const bool base_in_smem = maxc + 1 <= kBaseSmem;
     if (base_in_smem)
-        for (long long k = threadIdx.x; k <= a.maxc; k += blockDim.x) base_s[k] = a.base[k];
+        for (long long k = threadIdx.x; k <= maxc; k += blockDim.x) sh.base[k] = a.base[k];
     __syncthreads();
-    const unsigned long long* base = base_in_smem ? base_s : a.base;
-    GroupState& S = st_s[g];
-    TestSpec& spec = spec_s[g];
+    const unsigned long long* base = base_in_smem ? sh.base : a.base;
+    GroupState& S = sh.st[g];
+    TestSpec& spec = sh.spec[g];
 
     for (;;) {
         if (r == 0) {
-            const unsigned long long w = atomicAdd(a.next_item, 1ULL);
+            const unsigned long long w = atomicAdd(next_item, 1ULL);
             S.e = -1;
             if (w < total) {
-                long long lo = 0, hi = a.maxc - 1;   // pass k: largest k with base[k] <= w
+                long long lo = 0, hi = maxc - 1;   // pass k: largest k with base[k] <= w
                 while (lo < hi) {
                     const long long mid = (lo + hi + 1) >> 1;
                     if (base[mid] <= w) lo = mid; else hi = mid - 1;
                 }
                 const int e = a.sorted[w - base[lo]];
-                const long long r0 = lo * (long long)a.gs;
-                const long long tot = a.edges[e].total;
+                const long long tot = edges[e].total;
+                const long long cr = chunk_ranks(tot, a.gs);
+                const long long r0 = lo * cr;
                 S.e = e;
                 S.r0 = r0;
-                S.r1 = r0 + a.gs < tot ? r0 + a.gs : tot;
+                S.r1 = r0 + cr < tot ? r0 + cr : tot;
             }
         }
         Grp<G>::sync();
         const int e = S.e;
         if (e < 0) break;
-        const EdgeWork w = a.edges[e];
+        const EdgeWork w = edges[e];
         const ProblemDev& P = a.probs[w.prob];
         const long long r0 = S.r0, r1 = S.r1;
         for (long long rk = r0; rk < r1; ++rk) {
-            if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&a.min_accept[e]);
+            if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&min_accept[e]);
             Grp<G>::sync();
             if (!S.go) break;
-            const int res = run_rank<G>(a, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, red);
-            if (res == 1 && r == 0) atomicMin(&a.min_accept[e], (unsigned long long)rk);
+            const int res = run_rank<G>(a, d, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, sh.red);
+            if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)rk);
             if (res != 0) break;
         }
         Grp<G>::sync();
     }
 }
 
-__global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a, long long E)
+// Small-table class: the group size k_scan chose for this depth.
+__global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
+{
+    extern __shared__ int smem[];
+    __shared__ PoolShared sh;
+    if (!a.ctr->active) return;
+    switch (a.ctr->gsel) {
+        case 32: pool_body<32>(a, smem, sh); break;
+        case 64: pool_body<64>(a, smem, sh); break;
+        case 128: pool_body<128>(a, smem, sh); break;
+        default: pool_body<kTestThreads>(a, smem, sh); break;
+    }
+}
+
+// Big-table class: CTA groups.
+__global__ void __launch_bounds__(kTestThreads, 2) k_pool_big(PoolArgs a)
+{
+    extern __shared__ int smem[];
+    __shared__ PoolShared sh;
+    if (!a.ctr->active) return;
+    pool_body<kTestThreads>(a, smem, sh);
+}
+
+__global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
 {
     extern __shared__ int smem[];
     __shared__ TestSpec spec;
     __shared__ GroupState S;
     __shared__ double red[32];
+    const DepthCounters* ctr = a.ctr;
+    if (!ctr->active) return;
+    const int d = ctr->d;
+    const long long E = (long long)ctr->n_edges[a.cls];
+    const long long cb = class_base(ctr, a.cls, a.edge_cap);
     int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
     for (long long e = blockIdx.x; e < E; e += gridDim.x) {
-        const EdgeWork w = a.edges[e];
+        const EdgeWork w = a.edges[cb + e];
         const ProblemDev& P = a.probs[w.prob];
         for (long long rk = 0; rk < w.total; ++rk) {
-            const int res = run_rank<kTestThreads>(a, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
-            if (res == 1 && threadIdx.x == 0) a.min_accept[e] = (unsigned long long)rk;
+            const int res = run_rank<kTestThreads>(a, d, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
+            if (res == 1 && threadIdx.x == 0) a.min_accept[cb + e] = (unsigned long long)rk;
             if (res != 0) break;
         }
         __syncthreads();
@@ -393,40 +459,82 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a, long long
 
 // --------------------------------------------------------------------------
 __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __restrict__ edges,
-                        const unsigned long long* __restrict__ min_accept, long long E, int d,
-                        const long long* __restrict__ binom, int32_t* __restrict__ sep_pool,
-                        long long sep_cap, DepthCounters* ctr)
+                        const unsigned long long* __restrict__ min_accept, long long edge_cap,
+                        const long long* __restrict__ binom, int32_t* __restrict__ sep_pool, long long sep_cap,
+                        DepthCounters* ctr)
 {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const EdgeWork w = edges[e];
-    const unsigned long long ma = min_accept[e];
-    const bool rm = ma < (unsigned long long)w.total;
-    atomicAdd(&ctr->tests_oracle, rm ? ma + 1 : (unsigned long long)w.total);
-    if (!rm) return;
-    atomicAdd(&ctr->removed, 1ULL);
-    const ProblemDev P = probs[w.prob];
-    const long long n = P.n;
-    P.adj[w.i * n + w.j] = 0;
-    P.adj[w.j * n + w.i] = 0;
-    long long off = 0;
-    if (d > 0) {
-        off = (long long)atomicAdd(&ctr->sep_used, (unsigned long long)d);
-        if (off + d > sep_cap) {
-            atomicOr(&ctr->status, kStatusSepPool);
-        } else {
-            const bool xside = (long long)ma < w.cnt_i;
-            const int a = xside ? w.i : w.j;
-            const int posb = xside ? w.posj : w.posi;
-            const long long lr = xside ? (long long)ma : (long long)ma - w.cnt_i;
-            int pos[kMaxD];
-            unrank_lex(lr, P.deg[a] - 1, d, binom, pos);
-            const int32_t* nb = P.nbr + (long long)a * n;
-            for (int k = 0; k < d; ++k) sep_pool[off + k] = nb[pos[k] < posb ? pos[k] : pos[k] + 1];
+    if (!ctr->active) return;
+    const int d = ctr->d;
+    const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long e = k < n0 ? k : edge_cap - n1 + (k - n0);
+        const EdgeWork w = edges[e];
+        const unsigned long long ma = min_accept[e];
+        const bool rm = ma < (unsigned long long)w.total;
+        atomicAdd(&ctr->tests_oracle, rm ? ma + 1 : (unsigned long long)w.total);
+        if (!rm) continue;
+        atomicAdd(&ctr->removed, 1ULL);
+        const ProblemDev P = probs[w.prob];
+        const long long n = P.n;
+        P.adj[w.i * n + w.j] = 0;
+        P.adj[w.j * n + w.i] = 0;
+        long long off = 0;
+        if (d > 0) {
+            off = (long long)atomicAdd(&ctr->sep_used, (unsigned long long)d);
+            if (off + d > sep_cap) {
+                atomicOr(&ctr->status, kStatusSepPool);
+                off = 0;
+            } else {
+                const bool xside = (long long)ma < w.cnt_i;
+                const int a = xside ? w.i : w.j;
+                const int posb = xside ? w.posj : w.posi;
+                const long long lr = xside ? (long long)ma : (long long)ma - w.cnt_i;
+                int pos[kMaxD];
+                unrank_lex(lr, P.deg[a] - 1, d, binom, pos);
+                const int32_t* nb = P.nbr + (long long)a * n;
+                for (int q = 0; q < d; ++q) sep_pool[off + q] = nb[pos[q] < posb ? pos[q] : pos[q] + 1];
+            }
         }
+        P.sep_len[w.i * n + w.j] = d;
+        P.sep_off[w.i * n + w.j] = off;
     }
-    P.sep_len[w.i * n + w.j] = d;
-    P.sep_off[w.i * n + w.j] = off;
+}
+
+// End of a depth (one CTA): record it; stop when it had no edge to test (no
+// edge has a side with at least d candidates), when an error bit is set, or
+// when the next depth exceeds max_depth (>= 0); clear the per-depth counters,
+// the chunk histograms and the placement cursors for the next depth.
+__global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
+                            unsigned long long* cursor)
+{
+    if (!ctr->active) return;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int d = ctr->d;
+        const long long E = (long long)(ctr->n_edges[0] + ctr->n_edges[1]);
+        if (d < kMaxDepthRecords) {
+            rec[d].edges = E;
+            rec[d].tests = (long long)ctr->tests;
+            rec[d].tests_oracle = (long long)ctr->tests_oracle;
+            rec[d].removed = (long long)ctr->removed;
+        }
+        const int next = d + 1;
+        const bool stop = E == 0 || ctr->status != 0 || (max_depth >= 0 && next > max_depth) || next > kMaxD ||
+                          next >= kMaxDepthRecords;
+        for (int c = 0; c < 2; ++c)
+            ctr->n_edges[c] = ctr->maxc[c] = ctr->next_item[c] = ctr->total_items[c] = ctr->max_cells[c] = 0;
+        ctr->tests = ctr->tests_oracle = ctr->removed = 0;
+        ctr->gsel = 0;
+        ctr->d = next;
+        __threadfence();
+        ctr->active = stop ? 0 : 1;
+    }
+    const long long n = 2 * (kMaxPasses + 1);
+    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+        hist[k] = 0;
+        cursor[k] = 0;
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -487,60 +595,55 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
 // --------------------------------------------------------------------------
 // host launchers
 void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                     int total_vertices, cudaStream_t st)
+                     int total_vertices, const DepthCounters* ctr, cudaStream_t st)
 {
     const int warps = 8;
     k_snapshot<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(probs, vtx_prob, vtx_first,
-                                                                           total_vertices);
+                                                                           total_vertices, ctr);
 }
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                  int total_vertices, int d, int gs, const long long* binom, int brows, long long warp_cells_cap,
+                  int total_vertices, int gs, const long long* binom, int brows, long long warp_cells_cap,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
-                  cudaStream_t st)
+                  unsigned long long* hist, cudaStream_t st)
 {
     const int warps = 8;
     k_edges<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(
-        probs, vtx_prob, vtx_first, total_vertices, d, gs, binom, brows, warp_cells_cap, edges, min_accept,
-        edge_cap, ctr);
+        probs, vtx_prob, vtx_first, total_vertices, gs, binom, brows, warp_cells_cap, edges, min_accept, edge_cap,
+        ctr, hist);
 }
 
-void launch_order(const EdgeWork* edges, long long E, int gs, long long maxc, unsigned long long* hist,
-                  unsigned long long* alive, unsigned long long* base, unsigned long long* cursor,
-                  int32_t* sorted, unsigned long long* total_items, unsigned long long* next_item,
-                  cudaStream_t st)
+void launch_order(const EdgeWork* edges, long long edge_cap, int cls, int gs, DepthCounters* ctr,
+                  unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
+                  unsigned long long* cursor, int32_t* sorted, const long long groups[3], int forced_group,
+                  int grid, cudaStream_t st)
 {
-    cudaMemsetAsync(hist, 0, (maxc + 1) * sizeof(unsigned long long), st);
-    cudaMemsetAsync(cursor, 0, (maxc + 1) * sizeof(unsigned long long), st);
-    const int T = 256;
-    const unsigned blocks = (unsigned)((E + T - 1) / T);
-    k_chunk_hist<<<blocks, T, 0, st>>>(edges, E, gs, hist);
-    k_scan<<<1, 1024, 0, st>>>(hist, maxc, alive, base, total_items, next_item);
-    k_place<<<blocks, T, 0, st>>>(edges, E, gs, alive, cursor, sorted);
+    k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], forced_group);
+    k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, gs, ctr, alive, cursor, sorted);
 }
 
-void launch_pool(const PoolArgs& a, int group, int grid, size_t smem_bytes, cudaStream_t st)
+void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st)
 {
-    switch (group) {
-        case 32: k_pool<32><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
-        case 64: k_pool<64><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
-        case 128: k_pool<128><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
-        default: k_pool<kTestThreads><<<grid, kTestThreads, smem_bytes, st>>>(a); break;
-    }
+    if (cls == kClassWarp) k_pool_small<<<grid, kTestThreads, smem_bytes, st>>>(a);
+    else k_pool_big<<<grid, kTestThreads, smem_bytes, st>>>(a);
 }
 
-void launch_plain(const PoolArgs& a, long long E, int grid, size_t smem_bytes, cudaStream_t st)
+void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st)
 {
-    k_plain<<<grid, kTestThreads, smem_bytes, st>>>(a, E);
+    k_plain<<<grid, kTestThreads, smem_bytes, st>>>(a);
 }
 
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
-                  long long E, int d, const long long* binom, int32_t* sep_pool, long long sep_cap,
-                  DepthCounters* ctr, cudaStream_t st)
+                  long long edge_cap, const long long* binom, int32_t* sep_pool, long long sep_cap,
+                  DepthCounters* ctr, int grid, cudaStream_t st)
 {
-    const int T = 256;
-    k_apply<<<(unsigned)((E + T - 1) / T), T, 0, st>>>(probs, edges, min_accept, E, d, binom, sep_pool,
-                                                       sep_cap, ctr);
+    k_apply<<<grid, 256, 0, st>>>(probs, edges, min_accept, edge_cap, binom, sep_pool, sep_cap, ctr);
+}
+
+void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
+                      unsigned long long* cursor, cudaStream_t st)
+{
+    k_depth_end<<<1, 256, 0, st>>>(ctr, rec, max_depth, hist, cursor);
 }
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
@@ -555,25 +658,19 @@ cudaError_t set_kernel_smem(size_t max_smem)
 {
     cudaError_t e;
     const int b = (int)max_smem;
-    if ((e = cudaFuncSetAttribute(k_pool<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(k_pool<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(k_pool<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(k_pool<kTestThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool_small, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool_big, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     return cudaFuncSetAttribute(k_ci_tests, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
-int pool_blocks_per_sm(int group, size_t smem_bytes)
+int pool_blocks_per_sm(int cls, size_t smem_bytes)
 {
     int nb = 0;
-    switch (group) {
-        case 32: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<32>, kTestThreads, smem_bytes); break;
-        case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<64>, kTestThreads, smem_bytes); break;
-        case 128: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<128>, kTestThreads, smem_bytes); break;
-        default:
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool<kTestThreads>, kTestThreads, smem_bytes);
-            break;
-    }
+    if (cls == kClassWarp)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool_small, kTestThreads, smem_bytes);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool_big, kTestThreads, smem_bytes);
     return nb;
 }
 

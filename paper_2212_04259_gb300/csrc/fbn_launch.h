@@ -16,26 +16,28 @@ struct CiTestDesc {
 };
 
 void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                     int total_vertices, cudaStream_t st);
+                     int total_vertices, const DepthCounters* ctr, cudaStream_t st);
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                  int total_vertices, int d, int gs, const long long* binom, int brows, long long warp_cells_cap,
+                  int total_vertices, int gs, const long long* binom, int brows, long long warp_cells_cap,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
-                  cudaStream_t st);
-void launch_order(const EdgeWork* edges, long long E, int gs, long long maxc, unsigned long long* hist,
-                  unsigned long long* alive, unsigned long long* base, unsigned long long* cursor,
-                  int32_t* sorted, unsigned long long* total_items, unsigned long long* next_item,
-                  cudaStream_t st);
-void launch_pool(const PoolArgs& a, int group, int grid, size_t smem_bytes, cudaStream_t st);
-void launch_plain(const PoolArgs& a, long long E, int grid, size_t smem_bytes, cudaStream_t st);
+                  unsigned long long* hist, cudaStream_t st);
+void launch_order(const EdgeWork* edges, long long edge_cap, int cls, int gs, DepthCounters* ctr,
+                  unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
+                  unsigned long long* cursor, int32_t* sorted, const long long groups[3], int forced_group,
+                  int grid, cudaStream_t st);
+void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st);
+void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
-                  long long E, int d, const long long* binom, int32_t* sep_pool, long long sep_cap,
-                  DepthCounters* ctr, cudaStream_t st);
+                  long long edge_cap, const long long* binom, int32_t* sep_pool, long long sep_cap,
+                  DepthCounters* ctr, int grid, cudaStream_t st);
+void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
+                      unsigned long long* cursor, cudaStream_t st);
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
                      size_t smem_bytes, cudaStream_t st);
 cudaError_t set_kernel_smem(size_t max_smem);
 // Sets the message fbn_last_error(NULL) returns.
 void fbn_internal_set_error(const char* msg);
-int pool_blocks_per_sm(int group, size_t smem_bytes);
+int pool_blocks_per_sm(int cls, size_t smem_bytes);
 
 }  // namespace fbn
