@@ -57,7 +57,7 @@ def load_workload(name):
 
 
 def workload_config(name, w, args):
-    cfg = {"workload": name, "form": args.form, "group_size": args.gs or 1,
+    cfg = {"workload": name, "form": args.form, "group_size": args.gs or "per depth (1 or 4)",
            "l2": "flushed by a 256 MB device write before each timed step"}
     if w["kind"] == "single":
         n, N = w["data"].shape
@@ -312,8 +312,11 @@ def main():
                 else "k_plain", "kernel_ms_per_step": test_ms, "algorithmic_bytes_per_step": alg_bytes}
     roofline_gram = None
     if gram_used:
-        M, K = st["gram_rows"], meanN
-        flops = float(M) * M * K            # 2 M^2 N / 2
+        if w["kind"] == "single":
+            M = int(w["ar"].astype("int64").sum())
+            flops = float(M) * M * w["data"].shape[1]          # 2 M^2 N / 2
+        else:
+            flops = float(sum(int(a.astype("int64").sum()) ** 2 * d.shape[1] for d, a in w["probs"]))
         gms = st["gram_ms"]
         tf = flops / (gms / 1e3) / 1e12
         roofline_gram = {"bound": "tensor", "achieved": tf, "peak": fp8_peak, "unit": "TFLOP/s",

@@ -23,7 +23,6 @@ thread_local std::string g_create_error;
 
 constexpr size_t kSmemBytes = 108 * 1024;     // dynamic shared memory of a CTA test group (2 CTAs / SM)
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
-constexpr int kDefaultGs = 1;
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
 
 template <typename T>
@@ -98,6 +97,17 @@ struct Workspace {
     DepthRecord* h_rec = nullptr;                   // pinned
     int* h_active = nullptr;                        // pinned, one flag per depth
     long long gs_cells = 0;                         // cells per group of the global scratch
+    // one-hot Gram of a whole batch
+    uint8_t* gram_E = nullptr;                      // one-hot matrices, problem after problem
+    long long gram_E_cap = 0;
+    int32_t* gram_G = nullptr;                      // Grams, problem after problem
+    long long gram_G_cap = 0;
+    uint8_t* gram_maps = nullptr;                   // tensor maps, one per problem
+    long long gram_maps_cap = 0;
+    int4* gram_units = nullptr;
+    long long gram_units_cap = 0;
+    int gram_n_units = 0;
+    std::vector<uint8_t> h_maps;
     bool events = false;
 
     void release()
@@ -108,6 +118,7 @@ struct Workspace {
         if (h_ctr) cudaFreeHost(h_ctr);
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
         dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals);
+        dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units);
         if (events) {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
@@ -116,6 +127,8 @@ struct Workspace {
         dfree(d_rec);
         if (h_rec) cudaFreeHost(h_rec);
         if (h_active) cudaFreeHost(h_active);
+        h_maps.clear();
+        gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr;
         *this = Workspace();
     }
 };
@@ -153,10 +166,6 @@ struct fbn_handle {
     int Mp = 0;                         // M padded to the tile
     long long K = 0;                    // samples padded to the stage width
     int32_t* d_off = nullptr;           // [n] first one-hot row of each variable
-    uint8_t* d_E = nullptr;             // [Mp][K] E4M3 one-hot matrix
-    int32_t* d_G = nullptr;             // [Mp][Mp] INT32 Gram
-    int2* d_tiles = nullptr;
-    int n_tiles = 0;
     // results of the last skeleton
     bool learnt = false;
     bool sep_pending = false;           // separating sets still only on the device
@@ -329,41 +338,98 @@ int check_status(fbn_handle* h, unsigned status)
     return FBN_OK;
 }
 
-// Whether depth 0 of this handle runs as the one-hot Gram on tensor cores.
-bool use_gram(const fbn_handle* h, int k)
+// Whether depth 0 runs as the one-hot Gram on tensor cores.
+bool use_gram(fbn_handle* const* hs, int k)
 {
-    if (k != 1) return false;   // batches: many small problems, histogram path
+    const fbn_handle* h = hs[0];
     if (h->opt.depth0 == FBN_DEPTH0_GRAM) return true;
     if (h->opt.depth0 == FBN_DEPTH0_HIST) return false;
-    return h->M >= 512 && h->N >= 8192;
+    long long M = 0, Nmax = 0;
+    for (int p = 0; p < k; ++p) {
+        M += hs[p]->M;
+        Nmax = std::max<long long>(Nmax, hs[p]->N);
+    }
+    return M >= 512 && Nmax >= 4096;
 }
 
-// Build the one-hot matrix and its INT32 Gram (upper tile triangle) on the
-// handle's stream.  Buffers are allocated on first use and kept.
-int run_gram(fbn_handle* h, unsigned* d_status, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr)
+// Lay out the one-hot matrices and Grams of every problem in the workspace,
+// set the problems' pointers, and upload one tensor map per problem and the
+// work units (problem, tile pair, chunk), problem-major.
+int prepare_gram(fbn_handle* const* hs, int k, Workspace& ws, ProblemDev* P)
+{
+    fbn_handle* h = hs[0];
+    cudaStream_t st = h->stream;
+    long long e_total = 0, g_total = 0;
+    for (int p = 0; p < k; ++p) {
+        e_total += (long long)hs[p]->Mp * hs[p]->K;
+        g_total += (long long)hs[p]->Mp * hs[p]->Mp;
+    }
+    if (e_total > ws.gram_E_cap) {
+        dfree(ws.gram_E);
+        ws.gram_E = nullptr;
+        ws.gram_E_cap = 0;
+        CK(dalloc(&ws.gram_E, e_total));
+        ws.gram_E_cap = e_total;
+    }
+    if (g_total > ws.gram_G_cap) {
+        dfree(ws.gram_G);
+        ws.gram_G = nullptr;
+        ws.gram_G_cap = 0;
+        CK(dalloc(&ws.gram_G, g_total));
+        ws.gram_G_cap = g_total;
+    }
+    const size_t mb = tensor_map_bytes();
+    if ((long long)(k * mb) > ws.gram_maps_cap) {
+        dfree(ws.gram_maps);
+        ws.gram_maps = nullptr;
+        ws.gram_maps_cap = 0;
+        CK(dalloc(&ws.gram_maps, k * mb));
+        ws.gram_maps_cap = (long long)(k * mb);
+    }
+    ws.h_maps.assign(k * mb, 0);
+    std::vector<int4> units;
+    long long eo = 0, go = 0;
+    for (int p = 0; p < k; ++p) {
+        const fbn_handle* q = hs[p];
+        P[p].off = q->d_off;
+        P[p].onehot = ws.gram_E + eo;
+        P[p].gram = ws.gram_G + go;
+        P[p].onehot_ld = q->K;
+        P[p].gram_ld = q->Mp;
+        CK(encode_onehot_map(ws.h_maps.data() + p * mb, P[p].onehot, q->Mp, q->K));
+        const int T = q->Mp / 128, C = gram_chunks(q->K);
+        for (int c = 0; c < C; ++c)
+            for (int a = 0; a < T; ++a)
+                for (int b = a; b < T; ++b) units.push_back(make_int4(p, a, b, c));
+        eo += (long long)q->Mp * q->K;
+        go += (long long)q->Mp * q->Mp;
+    }
+    if ((long long)units.size() > ws.gram_units_cap) {
+        dfree(ws.gram_units);
+        ws.gram_units = nullptr;
+        ws.gram_units_cap = 0;
+        CK(dalloc(&ws.gram_units, units.size()));
+        ws.gram_units_cap = (long long)units.size();
+    }
+    ws.gram_n_units = (int)units.size();
+    CK(cudaMemcpyAsync(ws.gram_maps, ws.h_maps.data(), k * mb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ws.gram_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    return FBN_OK;
+}
+
+// One-hot matrices and their INT32 Grams (upper tile triangle) for the
+// problems already in ws.probs (prepared by prepare_gram).
+int run_gram(fbn_handle* h, Workspace& ws, int k, int total_vtx, unsigned* d_status, cudaEvent_t ev0 = nullptr,
+             cudaEvent_t ev1 = nullptr)
 {
     cudaStream_t st = h->stream;
-    if (!h->d_E) {
-        h->Mp = gram_rows_padded(h->M);
-        h->K = gram_samples_padded(h->N);
-        CK(dalloc(&h->d_E, (size_t)h->Mp * h->K));
-        CK(dalloc(&h->d_G, (size_t)h->Mp * h->Mp));
-        const int T = h->Mp / 128;
-        std::vector<int2> tiles;
-        for (int a = 0; a < T; ++a)
-            for (int b = a; b < T; ++b) tiles.push_back(make_int2(a, b));
-        h->n_tiles = (int)tiles.size();
-        CK(dalloc(&h->d_tiles, tiles.size()));
-        CK(cudaMemcpy(h->d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    }
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    // rows M..Mp stay zero; every row below M is rewritten each call
-    CK(cudaMemsetAsync(h->d_E + (size_t)h->M * h->K, 0, (size_t)(h->Mp - h->M) * h->K, st));
-    CK(launch_onehot(h->d_data, h->ld, h->n, (int)h->N, h->d_ar, h->d_off, h->d_E, h->K, st));
-    CK(cudaMemsetAsync(h->d_G, 0, (size_t)h->Mp * h->Mp * sizeof(int32_t), st));
+    CK(launch_zero_pad(ws.probs, k, st));
+    CK(launch_onehot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st));
+    CK(cudaMemsetAsync(ws.gram_G, 0, ws.gram_G_cap * sizeof(int32_t), st));
     if (ev0) CK(cudaEventRecord(ev0, st));
-    CK(launch_gram(h->d_E, h->Mp, h->K, h->d_G, h->d_tiles, h->n_tiles, sms, d_status, st));
+    CK(launch_gram(ws.gram_maps, ws.gram_units, ws.gram_n_units, ws.probs, sms, d_status, st));
     if (ev1) CK(cudaEventRecord(ev1, st));
     return FBN_OK;
 }
@@ -431,6 +497,12 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     }
     int rc = grow_workspace(h, ws, edge_cap, max_n, k, total_vtx);
     if (rc) return rc;
+    const bool plain = h->opt.form == FBN_FORM_PLAIN;
+    const bool gram = !plain && use_gram(hs, k);
+    if (gram) {
+        rc = prepare_gram(hs, k, ws, P.data());
+        if (rc) return rc;
+    }
     if (ws.sep_cap == 0) {
         rc = ensure_sep_pool(h, ws, 2 * edge_cap + 1024, 0, st);
         if (rc) return rc;
@@ -452,10 +524,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     int max_ar = 2;
     for (int p = 0; p < k; ++p) max_ar = std::max(max_ar, hs[p]->max_arity);
     const int grid_aux = dev_sms * 4;   // grid-stride helpers (ordering, removal)
-    const int gs = h->opt.group_size > 0 ? h->opt.group_size : kDefaultGs;
-    const bool plain = h->opt.form == FBN_FORM_PLAIN;
+    // ranks per chunk: fixed by the option, else chosen on the device per depth
+    const int gs_forced = plain ? 1 : h->opt.group_size;
+    const long long gs_edges = 8LL * grid_small * 8;   // live edges from which 4 ranks per claim pay
     const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
-    const bool gram = !plain && use_gram(h, k);
     const int forced = h->opt.group_threads;
     if (ws.crit_alpha != alpha) {
         CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
@@ -481,7 +553,6 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     base.binom = ws.binom;
     base.binom_rows = ws.brows;
     base.crit = ct;
-    base.gs = plain ? 1 : gs;
     base.alpha = alpha;
 
     int queued = 0;
@@ -489,8 +560,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         if (max_depth >= 0 && d > max_depth) break;
         CK(cudaEventRecord(ws.ev[d], st));
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
-        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, base.gs, ws.binom, ws.brows, wcap, ws.edges,
-                     ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
+        launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, gs_forced, gs_edges, ws.binom, ws.brows, wcap,
+                     ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
         launches += 2;
         // the big-table class can only be non-empty once max_arity^(d+2) tops
         // the small-table bound
@@ -499,11 +570,11 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         const bool big_possible = bound > wcap;
         CK(cudaEventRecord(ws.kev[2 * d], st));
         if (d == 0 && gram) {
-            rc = run_gram(h, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS], ws.kev[2 * FBN_MAX_DEPTHS + 1]);
+            rc = run_gram(h, ws, k, total_vtx, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS],
+                          ws.kev[2 * FBN_MAX_DEPTHS + 1]);
             if (rc) return rc;
-            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, h->d_G, h->Mp, h->d_off, ws.min_accept, ct, alpha,
-                                   ws.d_ctr, grid_aux, st));
-            launches += 3;
+            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr, grid_aux, st));
+            launches += 4;
         } else {
             for (int cls = 0; cls < 2; ++cls) {
                 if (cls == kClassCta && !big_possible) continue;
@@ -524,7 +595,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
                 unsigned long long* cls_base = ws.base + cls * ws.ord_cap;
                 a.base = cls_base;
                 a.sorted = ws.sorted;
-                launch_order(ws.edges, ws.edge_cap, cls, base.gs, ws.d_ctr, ws.hist + cls * ws.ord_cap,
+                launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap,
                              ws.alive + cls * ws.ord_cap, cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups,
                              forced, grid_aux, st);
                 launches += 2;
@@ -591,8 +662,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         float gms = 0.f;
         CK(cudaEventElapsedTime(&gms, ws.kev[2 * FBN_MAX_DEPTHS], ws.kev[2 * FBN_MAX_DEPTHS + 1]));
         stats.gram_ms = gms;
-        stats.gram_rows = h->M;
-        stats.gram_samples = h->K;
+        for (int p = 0; p < k; ++p) {
+            stats.gram_rows += hs[p]->M;
+            stats.gram_samples = std::max<int64_t>(stats.gram_samples, hs[p]->K);
+        }
     }
     stats.launches = launches;
     for (int p = 0; p < k; ++p) {
@@ -696,7 +769,7 @@ void free_handle(fbn_handle* h)
     dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
-    dfree(h->d_off); dfree(h->d_E); dfree(h->d_G); dfree(h->d_tiles);
+    dfree(h->d_off);
     if (h->h_ci) cudaFreeHost(h->h_ci);
     if (h->h_ci_out) cudaFreeHost(h->h_ci_out);
     if (h->h_status) cudaFreeHost(h->h_status);
@@ -824,6 +897,8 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
             M += arities[v];
         }
         h->M = M;
+        h->Mp = gram_rows_padded(M);
+        h->K = gram_samples_padded(n_samples);
         CKC(dalloc(&h->d_off, n_vars));
         CKC(cudaMemcpy(h->d_off, off.data(), n_vars * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
@@ -947,11 +1022,25 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
     const long long MM = (long long)h->M * h->M;
     if (cap < MM) return fail(h, FBN_EINVAL, "cap %lld < M*M = %lld", (long long)cap, MM);
     CK(cudaSetDevice(h->device));
-    CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
-    int rc = run_gram(h, h->d_status);
+    Workspace& ws = h->ws;
+    fbn_handle* hs[1] = {h};
+    int rc = grow_workspace(h, ws, (long long)h->n * (h->n - 1) / 2, h->n, 1, h->n);
     if (rc) return rc;
-    CK(launch_symmetrize(h->d_G, h->Mp, h->M, h->stream));
-    CK(cudaMemcpy2DAsync(counts, (size_t)h->M * sizeof(int32_t), h->d_G, (size_t)h->Mp * sizeof(int32_t),
+    ProblemDev P{};
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.deg = h->d_deg;
+    P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = h->n; P.N = (int32_t)h->N;
+    P.max_arity = h->max_arity;
+    rc = prepare_gram(hs, 1, ws, &P);
+    if (rc) return rc;
+    std::vector<int32_t> vp(h->n, 0), vf(1, 0);
+    CK(cudaMemcpyAsync(ws.probs, &P, sizeof P, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(ws.vtx_prob, vp.data(), h->n * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemcpyAsync(ws.vtx_first, vf.data(), sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), h->stream));
+    rc = run_gram(h, ws, 1, h->n, h->d_status);
+    if (rc) return rc;
+    CK(launch_symmetrize(P.gram, h->Mp, h->M, h->stream));
+    CK(cudaMemcpy2DAsync(counts, (size_t)h->M * sizeof(int32_t), P.gram, (size_t)h->Mp * sizeof(int32_t),
                          (size_t)h->M * sizeof(int32_t), (size_t)h->M, cudaMemcpyDefault, h->stream));
     CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));

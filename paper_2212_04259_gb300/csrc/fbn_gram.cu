@@ -152,17 +152,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v)
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Work unit of the Gram: problem, tile pair (ti <= tj), chunk of samples.
 struct GramArgs {
-    int32_t* G;           // [Mp][Mp] INT32 Gram, zeroed by the caller
-    const int2* tiles;    // upper-triangle tile pairs (ti <= tj)
-    int n_tiles;
-    int Mp;               // padded rows (multiple of 128)
-    int slices;           // padded samples / 128
-    int n_chunks;
+    const CUtensorMap* maps;    // [problems] tensor maps of the one-hot matrices (global memory)
+    const int4* units;          // [n_units] (problem, ti, tj, chunk)
+    const ProblemDev* probs;
+    int n_units;
     unsigned* status;
 };
 
-__global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant__ CUtensorMap tmap, GramArgs g)
+__global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -178,7 +177,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant_
     int* issued = reinterpret_cast<int*>(tmem_slot + 2);   // [kStages], producer thread only
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int U = g.n_tiles * g.n_chunks;
+    const int U = g.n_units;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -210,18 +209,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant_
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
+            int fenced = -1;
             for (int u = blockIdx.x; u < U && !*abort_flag; u += gridDim.x) {
-                const int c = u / g.n_tiles;
-                const int2 t = g.tiles[u - c * g.n_tiles];
-                const int kb0 = c * kSlicesPerChunk;
-                const int kb1 = min(kb0 + kSlicesPerChunk, g.slices);
+                const int4 t = g.units[u];
+                const CUtensorMap* map = g.maps + t.x;
+                if (t.x != fenced) {   // the host rewrites the maps between launches
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+                    fenced = t.x;
+                }
+                const int slices = (int)(g.probs[t.x].onehot_ld / kKSlice);
+                const int kb0 = t.w * kSlicesPerChunk;
+                const int kb1 = min(kb0 + kSlicesPerChunk, slices);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag, g.status)) break;
                     const uint32_t fb = smem_u32(&full[stage]);
                     const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
                     mbar_expect_tx(fb, kStageBytes);
-                    tma_load_2d(a, &tmap, fb, kb * kKSlice, t.x * kTile);
-                    tma_load_2d(a + kTileBytes, &tmap, fb, kb * kKSlice, t.y * kTile);
+                    tma_load_2d(a, map, fb, kb * kKSlice, t.y * kTile);
+                    tma_load_2d(a + kTileBytes, map, fb, kb * kKSlice, t.z * kTile);
                     issued[stage] += 1;
                     if (++stage == kStages) {
                         stage = 0;
@@ -239,9 +244,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant_
             uint32_t acc_phase = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < U && ok; u += gridDim.x) {
-                const int c = u / g.n_tiles;
-                const int kb0 = c * kSlicesPerChunk;
-                const int kb1 = min(kb0 + kSlicesPerChunk, g.slices);
+                const int4 t = g.units[u];
+                const int slices = (int)(g.probs[t.x].onehot_ld / kKSlice);
+                const int kb0 = t.w * kSlicesPerChunk;
+                const int kb1 = min(kb0 + kSlicesPerChunk, slices);
                 if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag, g.status)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * kTile);
@@ -277,23 +283,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant_
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int u = blockIdx.x; u < U; u += gridDim.x) {
-            const int c = u / g.n_tiles;
-            const int2 t = g.tiles[u - c * g.n_tiles];
+            const int4 t = g.units[u];
+            int32_t* G = g.probs[t.x].gram;
+            const long long ldg = g.probs[t.x].gram_ld;
             if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag, g.status)) break;
             tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kTile);
-            const long long row0 = (long long)t.x * kTile + warp * 32;
+            const long long row0 = (long long)t.y * kTile + warp * 32;
             for (int j0 = 0; j0 < kTile; j0 += 32) {
                 uint32_t v[32];
                 tmem_ld32(base + (uint32_t)j0, v);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) xp[lane * kStagePad + q] = __float2int_rn(__uint_as_float(v[q]));
                 __syncwarp();
-                int32_t* dst = g.G + row0 * g.Mp + (long long)t.y * kTile + j0 + lane;
+                int32_t* dst = G + row0 * ldg + (long long)t.z * kTile + j0 + lane;
 #pragma unroll 4
                 for (int r = 0; r < 32; ++r) {
                     const int val = xp[r * kStagePad + lane];
-                    if (val) atomicAdd(dst + (long long)r * g.Mp, val);
+                    if (val) atomicAdd(dst + (long long)r * ldg, val);
                 }
                 __syncwarp();
             }
@@ -323,16 +330,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(const __grid_constant_
     }
 }
 
-// One-hot matrix E: row off_v + x holds 0x38 (E4M3 1.0) where V_v = x, else
-// 0; samples at or beyond N (the padding of the store) are 0 for every row.
-__global__ void k_onehot(const uint8_t* __restrict__ data, long long ld, int n, int N, const uint8_t* __restrict__ ar,
-                         const int32_t* __restrict__ off, uint8_t* __restrict__ E, long long K)
+// One-hot matrix E of every problem: row off_v + x holds 0x38 (E4M3 1.0)
+// where V_v = x, else 0; samples at or beyond N (the padding of the store)
+// are 0 for every row.  One CTA per variable of the batch.
+__global__ void k_onehot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
+                         const int32_t* __restrict__ vtx_first, int total_vertices)
 {
-    const int v = blockIdx.y;
-    const int r = ar[v];
-    const uint4* row = reinterpret_cast<const uint4*>(data + (long long)v * ld);
+    const int g = blockIdx.x;
+    if (g >= total_vertices) return;
+    const int p = vtx_prob[g];
+    const ProblemDev& P = probs[p];
+    const int v = g - vtx_first[p];
+    const int r = P.ar[v];
+    const long long K = P.onehot_ld;
+    const int N = P.N;
+    const uint4* row = reinterpret_cast<const uint4*>(P.data + (long long)v * P.ld);
+    uint8_t* E = P.onehot + (long long)P.off[v] * K;
     const long long nvec = K / 16;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < nvec; q += (long long)gridDim.x * blockDim.x) {
+    for (long long q = threadIdx.x; q < nvec; q += blockDim.x) {
         uint4 w = row[q];
         const long long s0 = q * 16;
         uint32_t keep[4];
@@ -351,39 +366,43 @@ __global__ void k_onehot(const uint8_t* __restrict__ data, long long ld, int n, 
             o.y = __vcmpeq4(w.y, rep) & 0x38383838u & keep[1];
             o.z = __vcmpeq4(w.z, rep) & 0x38383838u & keep[2];
             o.w = __vcmpeq4(w.w, rep) & 0x38383838u & keep[3];
-            reinterpret_cast<uint4*>(E + (long long)(off[v] + x) * K)[q] = o;
+            reinterpret_cast<uint4*>(E + (long long)x * K)[q] = o;
         }
     }
 }
 
-__device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, long long e,
-                                            const ProblemDev* __restrict__ probs, const int32_t* __restrict__ G,
-                                            int Mp, const int32_t* __restrict__ off,
-                                            unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                            double alpha, DepthCounters* ctr)
+// Decision of one depth-0 pair from its block of the Gram (row sums, column
+// sums and the total from the block itself).  R bounds the arities so that
+// the sums live in registers.
+template <int R>
+__device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, int rx, int ry, long long e,
+                                              unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
+                                              double alpha, DepthCounters* ctr)
 {
-    const EdgeWork w = edges[e];
-    const ProblemDev& P = probs[w.prob];
-    const int rx = P.ar[w.i], ry = P.ar[w.j];
-    const int32_t* T = G + (long long)off[w.i] * Mp + off[w.j];
-    int rs[kMaxArityPairs], cs[kMaxArityPairs];
+    int rs[R], cs[R];
     int tot = 0;
-    for (int x = 0; x < rx; ++x) rs[x] = 0;
-    for (int y = 0; y < ry; ++y) cs[y] = 0;
-    for (int x = 0; x < rx; ++x)
-        for (int y = 0; y < ry; ++y) {
-            const int nxy = T[(long long)x * Mp + y];
-            rs[x] += nxy;
-            cs[y] += nxy;
-            tot += nxy;
-        }
+#pragma unroll
+    for (int q = 0; q < R; ++q) rs[q] = cs[q] = 0;
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+        for (int y = 0; y < R; ++y)
+            if (x < rx && y < ry) {
+                const int nxy = T[(long long)x * Mp + y];
+                rs[x] += nxy;
+                cs[y] += nxy;
+                tot += nxy;
+            }
     // terms with FP32 logs summed in FP64 (each term within 3.2e-7 of its
     // magnitude); exact FP64 only when crit lies inside the error band
     const long long df = (long long)(rx - 1) * (ry - 1);
     const double c = crit_get(crit, df, alpha, &ctr->status);
     double acc = 0.0, mag = 0.0;
-    for (int x = 0; x < rx; ++x)
-        for (int y = 0; y < ry; ++y) {
+#pragma unroll
+    for (int x = 0; x < R; ++x)
+#pragma unroll
+        for (int y = 0; y < R; ++y) {
+            if (x >= rx || y >= ry) continue;
             const int n = T[(long long)x * Mp + y];
             if (n == 0) continue;
             const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
@@ -393,7 +412,7 @@ __device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, 
             acc += (double)((float)n * L);
             mag += fabs((double)((float)n * L));
         }
-    double g2 = 2.0 * acc;
+    const double g2 = 2.0 * acc;
     const double err = 2.0 * 2.0 * 3.2e-7 * mag * 1.0001 + 1e-9;
     bool accept;
     if (g2 + err < c) {
@@ -402,8 +421,11 @@ __device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, 
         accept = false;
     } else {
         double ex = 0.0;
-        for (int x = 0; x < rx; ++x)
-            for (int y = 0; y < ry; ++y) {
+#pragma unroll
+        for (int x = 0; x < R; ++x)
+#pragma unroll
+            for (int y = 0; y < R; ++y) {
+                if (x >= rx || y >= ry) continue;
                 const int n = T[(long long)x * Mp + y];
                 if (n == 0) continue;
                 const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
@@ -412,23 +434,73 @@ __device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, 
         accept = 2.0 * ex < c;
     }
     if (accept) min_accept[e] = 0;
-    atomicAdd(&ctr->tests, 1ULL);
 }
 
+// Arities above 8: the sums are recomputed from the block (no local arrays).
+__device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp, int rx, int ry, long long e,
+                                                 unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
+                                                 double alpha, DepthCounters* ctr)
+{
+    long long tot = 0;
+    for (int x = 0; x < rx; ++x)
+        for (int y = 0; y < ry; ++y) tot += T[(long long)x * Mp + y];
+    const long long df = (long long)(rx - 1) * (ry - 1);
+    const double c = crit_get(crit, df, alpha, &ctr->status);
+    double ex = 0.0;
+    for (int x = 0; x < rx; ++x) {
+        long long rsx = 0;
+        for (int y = 0; y < ry; ++y) rsx += T[(long long)x * Mp + y];
+        for (int y = 0; y < ry; ++y) {
+            const int n = T[(long long)x * Mp + y];
+            if (n == 0) continue;
+            long long csy = 0;
+            for (int xx = 0; xx < rx; ++xx) csy += T[(long long)xx * Mp + y];
+            const long long a = (long long)n * tot, b = rsx * csy;
+            ex += (double)n * log1p((double)(a - b) / (double)b);
+        }
+    }
+    if (2.0 * ex < c) min_accept[e] = 0;
+}
+
+__device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, long long e,
+                                            const ProblemDev* __restrict__ probs,
+                                            unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
+                                            double alpha, DepthCounters* ctr)
+{
+    const EdgeWork w = edges[e];
+    const ProblemDev& P = probs[w.prob];
+    const int rx = P.ar[w.i], ry = P.ar[w.j];
+    const long long Mp = P.gram_ld;
+    const int32_t* T = P.gram + (long long)P.off[w.i] * Mp + P.off[w.j];
+    if (rx <= 4 && ry <= 4) pair_decide_r<4>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
+    else if (rx <= 8 && ry <= 8) pair_decide_r<8>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
+    else pair_decide_wide(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
+}
 
 // Depth-0 decisions from the Gram: one thread per edge (i<j) of both classes
 // of the edge list (class 0 at the front of the array, class 1 at the back).
 __global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long edge_cap,
-                               const ProblemDev* __restrict__ probs, const int32_t* __restrict__ G, int Mp,
-                               const int32_t* __restrict__ off, unsigned long long* __restrict__ min_accept,
+                               const ProblemDev* __restrict__ probs, unsigned long long* __restrict__ min_accept,
                                CritTableDev crit, double alpha, DepthCounters* ctr)
 {
     if (!ctr->active) return;
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
          k += (long long)gridDim.x * blockDim.x)
-        pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, G, Mp, off, min_accept, crit, alpha, ctr);
+        pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, min_accept, crit, alpha, ctr);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctr->tests, (unsigned long long)(n0 + n1));   // one test per pair
 }
+// Zero the pad rows M..Mp of every problem's one-hot matrix (one CTA per
+// problem); rows below M are rewritten by k_onehot on every call.
+__global__ void k_zero_pad(const ProblemDev* __restrict__ probs)
+{
+    const ProblemDev& P = probs[blockIdx.x];
+    const long long M = (long long)P.off[P.n - 1] + P.ar[P.n - 1];
+    uint4* E = reinterpret_cast<uint4*>(P.onehot + M * P.onehot_ld);
+    const long long n = (P.gram_ld - M) * P.onehot_ld / 16;
+    for (long long q = threadIdx.x; q < n; q += blockDim.x) E[q] = make_uint4(0, 0, 0, 0);
+}
+
 // Mirror the upper block triangle into the lower one (row < col -> col, row).
 __global__ void k_symmetrize(int32_t* G, int Mp, int M)
 {
@@ -460,52 +532,62 @@ int gram_rows_padded(int M) { return (M + kTile - 1) / kTile * kTile; }
 
 long long gram_samples_padded(long long N) { return (N + kKSlice - 1) / kKSlice * kKSlice; }
 
-cudaError_t launch_onehot(const uint8_t* data, long long ld, int n, int N, const uint8_t* ar, const int32_t* off,
-                          uint8_t* E, long long K, cudaStream_t st)
+cudaError_t launch_onehot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
+                          int total_vertices, cudaStream_t st)
 {
-    dim3 grid((unsigned)std::min<long long>((K / 16 + 255) / 256, 64), (unsigned)n);
-    k_onehot<<<grid, 256, 0, st>>>(data, ld, n, N, ar, off, E, K);
+    k_onehot<<<total_vertices, 256, 0, st>>>(probs, vtx_prob, vtx_first, total_vertices);
     return cudaGetLastError();
 }
 
-// Gram of the one-hot matrix E [Mp][K] (K a multiple of 128) into G [Mp][Mp]
-// (upper tile triangle; G must be zero).  tiles: device array of the
-// Mp/128 (Mp/128 + 1)/2 tile pairs.
-cudaError_t launch_gram(const uint8_t* E, int Mp, long long K, int32_t* G, const int2* tiles, int n_tiles,
-                        int num_sms, unsigned* status, cudaStream_t st)
+cudaError_t launch_zero_pad(const ProblemDev* probs, int nprob, cudaStream_t st)
+{
+    k_zero_pad<<<nprob, 256, 0, st>>>(probs);
+    return cudaGetLastError();
+}
+
+cudaError_t encode_onehot_map(void* map, const uint8_t* E, int Mp, long long K)
 {
     auto encode = encode_fn();
     if (!encode) return cudaErrorNotSupported;
-    CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)Mp};
     cuuint64_t strides[1] = {(cuuint64_t)K};
     cuuint32_t box[2] = {(cuuint32_t)kKSlice, (cuuint32_t)kTile};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(E), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(E),
+                        dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+int gram_chunks(long long K) { return (int)((K / kKSlice + kSlicesPerChunk - 1) / kSlicesPerChunk); }
+
+// Gram of every problem's one-hot matrix over the given work units; each
+// problem's Gram must be zero.  maps: device array of tensor maps (one per
+// problem, 64-byte aligned).
+cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const ProblemDev* probs, int num_sms,
+                        unsigned* status, cudaStream_t st)
+{
     GramArgs g;
-    g.G = G;
-    g.tiles = tiles;
-    g.n_tiles = n_tiles;
-    g.Mp = Mp;
-    g.slices = (int)(K / kKSlice);
-    g.n_chunks = (g.slices + kSlicesPerChunk - 1) / kSlicesPerChunk;
+    g.maps = reinterpret_cast<const CUtensorMap*>(maps);
+    g.units = units;
+    g.probs = probs;
+    g.n_units = n_units;
     g.status = status;
     cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem);
     if (e != cudaSuccess) return e;
-    const int units = n_tiles * g.n_chunks;
-    const int grid = units < num_sms ? units : num_sms;
-    k_gram<<<grid, kGramThreads, kGramSmem, st>>>(map, g);
+    const int grid = n_units < num_sms ? n_units : num_sms;
+    if (grid <= 0) return cudaSuccess;
+    k_gram<<<grid, kGramThreads, kGramSmem, st>>>(g);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs, const int32_t* G,
-                                int Mp, const int32_t* off, unsigned long long* min_accept, const CritTableDev& crit,
-                                double alpha, DepthCounters* ctr, int grid, cudaStream_t st)
+cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs,
+                                unsigned long long* min_accept, const CritTableDev& crit, double alpha,
+                                DepthCounters* ctr, int grid, cudaStream_t st)
 {
-    k_pairs_decide<<<grid, 256, 0, st>>>(edges, edge_cap, probs, G, Mp, off, min_accept, crit, alpha, ctr);
+    k_pairs_decide<<<grid, 256, 0, st>>>(edges, edge_cap, probs, min_accept, crit, alpha, ctr);
     return cudaGetLastError();
 }
 

@@ -12,13 +12,17 @@ namespace fbn {
 size_t gram_smem_bytes();
 int gram_rows_padded(int M);
 long long gram_samples_padded(long long N);
-cudaError_t launch_onehot(const uint8_t* data, long long ld, int n, int N, const uint8_t* ar, const int32_t* off,
-                          uint8_t* E, long long K, cudaStream_t st);
-cudaError_t launch_gram(const uint8_t* E, int Mp, long long K, int32_t* G, const int2* tiles, int n_tiles,
-                        int num_sms, unsigned* status, cudaStream_t st);
-cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs, const int32_t* G,
-                                int Mp, const int32_t* off, unsigned long long* min_accept, const CritTableDev& crit,
-                                double alpha, DepthCounters* ctr, int grid, cudaStream_t st);
+cudaError_t launch_onehot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
+                          int total_vertices, cudaStream_t st);
+cudaError_t launch_zero_pad(const ProblemDev* probs, int nprob, cudaStream_t st);
+cudaError_t encode_onehot_map(void* map, const uint8_t* E, int Mp, long long K);
+size_t tensor_map_bytes();
+int gram_chunks(long long K);
+cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const ProblemDev* probs, int num_sms,
+                        unsigned* status, cudaStream_t st);
+cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs,
+                                unsigned long long* min_accept, const CritTableDev& crit, double alpha,
+                                DepthCounters* ctr, int grid, cudaStream_t st);
 cudaError_t launch_symmetrize(int32_t* G, int Mp, int M, cudaStream_t st);
 
 }  // namespace fbn

@@ -39,6 +39,12 @@ struct ProblemDev {
     int32_t N;
     int32_t max_arity;
     int32_t pad;
+    // one-hot Gram of depth 0 (unused when depth 0 runs on the histogram path)
+    const int32_t* off;    // [n] first one-hot row of each variable
+    uint8_t* onehot;       // [gram_ld][onehot_ld] E4M3 one-hot rows
+    int32_t* gram;         // [gram_ld][gram_ld] INT32 Gram (upper tile triangle)
+    int64_t onehot_ld;     // padded samples (multiple of 128)
+    int64_t gram_ld;       // padded rows Mp (multiple of 128)
 };
 
 // One edge i<j of the current depth with its rank space: ranks [0, cnt_i) are
@@ -73,7 +79,8 @@ struct DepthCounters {
     int active;                         // 1 while Algorithm 1 continues (persists)
     int gsel;                           // group size of the small-table class this depth
     int need_cells;                     // largest table that missed the global scratch (persists)
-    int pad;
+    int gs;                             // ranks per chunk this depth (set by k_edges)
+    unsigned long long adj_ends;        // sum of the snapshot degrees (twice the live edges)
 };
 
 // Per-depth record written by k_depth_end.
@@ -121,7 +128,7 @@ struct PoolArgs {
     long long gscratch_ints;
     CritTableDev crit;
     int32_t cls;
-    int32_t gs;
+    int32_t pad;
     int32_t smem_ints;
     int32_t binom_rows;
     double alpha;

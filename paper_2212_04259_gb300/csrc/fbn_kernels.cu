@@ -34,7 +34,7 @@ namespace fbn {
 
 // --------------------------------------------------------------------------
 __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
-                           const int32_t* __restrict__ vtx_first, int total_vertices, const DepthCounters* ctr)
+                           const int32_t* __restrict__ vtx_first, int total_vertices, DepthCounters* ctr)
 {
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -52,7 +52,10 @@ __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* 
         if (a) out[count + __popc(m & ((1u << lane) - 1u))] = j;
         count += __popc(m);
     }
-    if (lane == 0) P.deg[v] = count;
+    if (lane == 0) {
+        P.deg[v] = count;
+        atomicAdd((unsigned long long*)&ctr->adj_ends, (unsigned long long)count);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -64,7 +67,7 @@ __device__ __forceinline__ long long binom_sat(const long long* B, int brows, in
 }
 
 __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
-                        const int32_t* __restrict__ vtx_first, int total_vertices, int gs,
+                        const int32_t* __restrict__ vtx_first, int total_vertices, int gs_forced, long long gs_edges,
                         const long long* __restrict__ binom, int brows, long long warp_cells_cap,
                         EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
                         long long edge_cap, DepthCounters* ctr, unsigned long long* __restrict__ hist)
@@ -73,6 +76,10 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
     const int lane = threadIdx.x & 31;
     if (g >= total_vertices || !ctr->active) return;
     const int d = ctr->d;
+    // ranks per chunk: 1 while the live edges are few against the groups
+    // (latency of a single test dominates), 4 when there are many (fewer claims)
+    const int gs = gs_forced > 0 ? gs_forced : ((long long)(ctr->adj_ends / 2) >= gs_edges ? 4 : 1);
+    if (g == 0 && lane == 0) ctr->gs = gs;
     const int p = vtx_prob[g];
     const ProblemDev P = probs[p];
     const int i = g - vtx_first[p];
@@ -103,6 +110,11 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
                 cells *= (unsigned long long)P.max_arity;
         }
         const int cls = cells <= (unsigned long long)warp_cells_cap ? kClassWarp : kClassCta;
+        {   // chunk-count histogram of each class: one atomic per distinct bin in the warp
+            const long long bin = total > 0 ? (long long)cls * (kMaxPasses + 1) + chunk_count(total, gs) : -1;
+            const unsigned same = __match_any_sync(0xffffffffu, bin);
+            if (bin >= 0 && lane == __ffs(same) - 1) atomicAdd(&hist[bin], (unsigned long long)__popc(same));
+        }
         for (int c = 0; c < 2; ++c) {
             const bool take = total > 0 && cls == c;
             const unsigned m = __ballot_sync(0xffffffffu, take);
@@ -130,7 +142,6 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
             edges[e] = w;
             min_accept[e] = (unsigned long long)total;
             const unsigned long long ch = (unsigned long long)chunk_count(total, gs);
-            atomicAdd(&hist[c * (kMaxPasses + 1) + ch], 1ULL);   // chunk-count histogram of the class
             mc[c] = ch > mc[c] ? ch : mc[c];
             mcell[c] = cells > mcell[c] ? cells : mcell[c];
         }
@@ -240,11 +251,12 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, Dep
     }
 }
 
-__global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, int cls, int gs,
+__global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, int cls,
                         const DepthCounters* ctr, const unsigned long long* __restrict__ alive,
                         unsigned long long* __restrict__ cursor, int32_t* __restrict__ sorted)
 {
     if (!ctr->active) return;
+    const int gs = ctr->gs;
     const long long E = (long long)ctr->n_edges[cls];
     const EdgeWork* ed = edges + class_base(ctr, cls, edge_cap);
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
@@ -258,6 +270,7 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, 
 // Per-group state of a worker, in shared memory.
 struct GroupState {
     long long r0, r1;
+    unsigned long long tests;
     int e;
     int go;
     double crit;
@@ -333,7 +346,7 @@ __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemD
     if (Grp<G>::rank() == 0) {
         const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
         S.crit = crit_get(a.crit, df, a.alpha, status);
-        atomicAdd(&a.ctr->tests, 1ULL);
+        S.tests += 1;   // flushed to the depth counter when the group leaves the pool
     }
     Grp<G>::sync();
     return grp_decide<G>(spec, T, M, S.crit, red) ? 1 : 0;
@@ -360,6 +373,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     const EdgeWork* edges = a.edges + cb;
     unsigned long long* min_accept = a.min_accept + cb;
     unsigned long long* next_item = &a.ctr->next_item[a.cls];
+    const int gs = ctr->gs;
     const int g = Grp<G>::gid();
     const int r = Grp<G>::rank();
     const long long slice_ints = a.smem_ints / NG;
@@ -372,6 +386,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     const unsigned long long* base = base_in_smem ? sh.base : a.base;
     GroupState& S = sh.st[g];
     TestSpec& spec = sh.spec[g];
+    if (r == 0) S.tests = 0;
 
     for (;;) {
         if (r == 0) {
@@ -385,7 +400,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
                 }
                 const int e = a.sorted[w - base[lo]];
                 const long long tot = edges[e].total;
-                const long long cr = chunk_ranks(tot, a.gs);
+                const long long cr = chunk_ranks(tot, gs);
                 const long long r0 = lo * cr;
                 S.e = e;
                 S.r0 = r0;
@@ -408,6 +423,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
         }
         Grp<G>::sync();
     }
+    if (r == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
 }
 
 // Small-table class: the group size k_scan chose for this depth.
@@ -445,6 +461,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
     const long long E = (long long)ctr->n_edges[a.cls];
     const long long cb = class_base(ctr, a.cls, a.edge_cap);
     int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
+    if (threadIdx.x == 0) S.tests = 0;
     for (long long e = blockIdx.x; e < E; e += gridDim.x) {
         const EdgeWork w = a.edges[cb + e];
         const ProblemDev& P = a.probs[w.prob];
@@ -455,6 +472,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
 }
 
 // --------------------------------------------------------------------------
@@ -466,15 +484,16 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
     if (!ctr->active) return;
     const int d = ctr->d;
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
+    unsigned long long my_tests = 0, my_removed = 0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
          k += (long long)gridDim.x * blockDim.x) {
         const long long e = k < n0 ? k : edge_cap - n1 + (k - n0);
         const EdgeWork w = edges[e];
         const unsigned long long ma = min_accept[e];
         const bool rm = ma < (unsigned long long)w.total;
-        atomicAdd(&ctr->tests_oracle, rm ? ma + 1 : (unsigned long long)w.total);
+        my_tests += rm ? ma + 1 : (unsigned long long)w.total;
         if (!rm) continue;
-        atomicAdd(&ctr->removed, 1ULL);
+        my_removed += 1;
         const ProblemDev P = probs[w.prob];
         const long long n = P.n;
         P.adj[w.i * n + w.j] = 0;
@@ -498,6 +517,15 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
         }
         P.sep_len[w.i * n + w.j] = d;
         P.sep_off[w.i * n + w.j] = off;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_tests += __shfl_xor_sync(0xffffffffu, my_tests, o);
+        my_removed += __shfl_xor_sync(0xffffffffu, my_removed, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_tests) atomicAdd(&ctr->tests_oracle, my_tests);
+        if (my_removed) atomicAdd(&ctr->removed, my_removed);
     }
 }
 
@@ -526,6 +554,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
             ctr->n_edges[c] = ctr->maxc[c] = ctr->next_item[c] = ctr->total_items[c] = ctr->max_cells[c] = 0;
         ctr->tests = ctr->tests_oracle = ctr->removed = 0;
         ctr->gsel = 0;
+        ctr->adj_ends = 0;
         ctr->d = next;
         __threadfence();
         ctr->active = stop ? 0 : 1;
@@ -595,7 +624,7 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
 // --------------------------------------------------------------------------
 // host launchers
 void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                     int total_vertices, const DepthCounters* ctr, cudaStream_t st)
+                     int total_vertices, DepthCounters* ctr, cudaStream_t st)
 {
     const int warps = 8;
     k_snapshot<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(probs, vtx_prob, vtx_first,
@@ -603,23 +632,24 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
 }
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                  int total_vertices, int gs, const long long* binom, int brows, long long warp_cells_cap,
+                  int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
+                  long long warp_cells_cap,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st)
 {
     const int warps = 8;
     k_edges<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(
-        probs, vtx_prob, vtx_first, total_vertices, gs, binom, brows, warp_cells_cap, edges, min_accept, edge_cap,
-        ctr, hist);
+        probs, vtx_prob, vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, edges,
+        min_accept, edge_cap, ctr, hist);
 }
 
-void launch_order(const EdgeWork* edges, long long edge_cap, int cls, int gs, DepthCounters* ctr,
+void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
                   unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
                   unsigned long long* cursor, int32_t* sorted, const long long groups[3], int forced_group,
                   int grid, cudaStream_t st)
 {
     k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], forced_group);
-    k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, gs, ctr, alive, cursor, sorted);
+    k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, ctr, alive, cursor, sorted);
 }
 
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st)

@@ -16,12 +16,13 @@ struct CiTestDesc {
 };
 
 void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                     int total_vertices, const DepthCounters* ctr, cudaStream_t st);
+                     int total_vertices, DepthCounters* ctr, cudaStream_t st);
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
-                  int total_vertices, int gs, const long long* binom, int brows, long long warp_cells_cap,
+                  int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
+                  long long warp_cells_cap,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st);
-void launch_order(const EdgeWork* edges, long long edge_cap, int cls, int gs, DepthCounters* ctr,
+void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
                   unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
                   unsigned long long* cursor, int32_t* sorted, const long long groups[3], int forced_group,
                   int grid, cudaStream_t st);

@@ -86,3 +86,24 @@ def test_depth0_gram_skeleton_matches_oracle(F):
         st = F.fbn_get_stats(h)
         if not ref.near:
             assert st["tests_oracle"] == ref.tests and st["tests"][0] == ref.tests[0]
+
+
+def test_batched_gram_skeletons_match_oracle(F):
+    # a batch large enough to run depth 0 on the tensor cores, problems of
+    # different sizes and sample counts
+    probs = bnsynth.batched_workload(5, first=10, n_range=(60, 140), samples_range=(3000, 12000))
+    hs = [F.fbn_create(d, a, depth0="gram") for d, a, _ in probs]
+    adjs = F.fbn_learn_skeleton_batch(hs, 0.05, 1)
+    st = F.fbn_get_stats(hs[0])
+    assert st["gram_ms"] > 0
+    for (d, a, _), h, adj in zip(probs, hs, adjs):
+        ref = oracle.pc_stable(d, a, 0.05, 1)
+        hard, _, _ = compare(adj, F.fbn_export_sepsets(h), ref)
+        assert not hard
+    # the same problems one at a time give the same counts
+    for (d, a, _), h in zip(probs[:2], hs[:2]):
+        G = F.fbn_pairwise_counts(h)
+        off = _offsets(a)
+        for i, j in [(0, 1), (2, len(a) - 1)]:
+            blk = G[off[i]:off[i] + a[i], off[j]:off[j] + a[j]].ravel()
+            assert np.array_equal(blk, oracle.ci_table(d, a, i, j))
