@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--workload", default="mid")
     ap.add_argument("--form", choices=["pool", "plain"], default="pool")
     ap.add_argument("--gs", type=int, default=0)
+    ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -229,11 +230,13 @@ def main():
     gs = args.gs
     if w["kind"] == "single":
         data_dev = torch.from_numpy(w["data"]).cuda()
-        handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local)]
+        handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local,
+                                group_threads=args.group_threads)]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((w["data"].shape[0],) * 2, dtype=torch.uint8, device="cuda")]
     else:
-        handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local)
+        handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local,
+                                group_threads=args.group_threads)
                    for d, a in w["probs"]]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8, device="cuda") for d, _ in w["probs"]]

@@ -520,7 +520,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     // CTAs of the small-table pool (any group size) and of the big-table pool
     const int grid_small = dev_sms * std::max(1, pool_blocks_per_sm(kClassWarp, kWarpSmemBytes));
     const int grid_big = dev_sms * std::max(1, pool_blocks_per_sm(kClassCta, kSmemBytes));
-    const long long groups[3] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2};
+    const long long groups[4] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2,
+                                 (long long)grid_small};
+    double mean_n = 0;
+    for (int p = 0; p < k; ++p) mean_n += (double)hs[p]->N / k;
     int max_ar = 2;
     for (int p = 0; p < k; ++p) max_ar = std::max(max_ar, hs[p]->max_arity);
     const int grid_aux = dev_sms * 4;   // grid-stride helpers (ordering, removal)
@@ -597,7 +600,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
                 a.sorted = ws.sorted;
                 launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap,
                              ws.alive + cls * ws.ord_cap, cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups,
-                             forced, grid_aux, st);
+                             mean_n, forced, grid_aux, st);
                 launches += 2;
                 launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
                 launches += 1;

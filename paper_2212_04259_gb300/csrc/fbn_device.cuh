@@ -240,7 +240,7 @@ __device__ __forceinline__ void grp_sum2(double& a, double& b, double* red)
     }
 }
 
-enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3 };
+enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3, kLane16 = 4 };
 
 template <int MODE>
 __device__ __forceinline__ void bump(int* base, unsigned idx)
@@ -249,6 +249,7 @@ __device__ __forceinline__ void bump(int* base, unsigned idx)
     // the update is still a shared-memory reduction (red.shared.add) rather
     // than load-add-store, so consecutive samples do not wait on each other
     if (MODE == kLane) atomicAdd(base + idx * 32u, 1);
+    else if (MODE == kLane16) atomicAdd(base + (idx >> 1) * 32u, 1 << ((idx & 1u) << 4));   // two 16-bit counters
     else atomicAdd(base + idx, 1);
 }
 
@@ -408,11 +409,16 @@ __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 }
 
 // Shared-memory ints needed by each counting strategy for a table of C cells
-// (marg = marginal entries); kGlobal when none fits.
+// (marg = marginal entries); kGlobal when none fits.  kLane16 (warp groups)
+// packs two lane-private counters per word: a lane counts at most
+// N / 32 + 16 samples, which must stay below 2^16.  Its extra zeroing and
+// merge only pay off when the sample loop is long (measured: a gain at
+// N = 100,000, a loss at N around 12,500), hence N >= 32768.
 template <int G>
-__device__ __forceinline__ int pick_mode(long long C, long long marg, long long slice_ints)
+__device__ __forceinline__ int pick_mode(long long C, long long marg, long long slice_ints, int N)
 {
     if (C * G + C + marg <= slice_ints) return kLane;
+    if (G == 32 && N >= 32768 && N / 32 + 32 < 65536 && (C + 1) / 2 * 32 + C + marg <= slice_ints) return kLane16;
     if (Grp<G>::kWarps > 1 && C * Grp<G>::kWarps + marg <= slice_ints) return kWarp;
     if (C + marg <= slice_ints) return kShared;
     return kGlobal;
@@ -428,24 +434,36 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
     const long long C = s.cells;
     const long long nz = C / (s.rx * s.ry);
     const long long marg = nz * (s.rx + s.ry + 1);
-    const int mode = pick_mode<G>(C, marg, slice_ints);
+    const int mode = pick_mode<G>(C, marg, slice_ints, s.N);
     if (mode == kGlobal && (gtab == nullptr || C + marg > gtab_ints)) return nullptr;
     const int r = Grp<G>::rank();
     const int lane = threadIdx.x & 31;
     const int warp = r >> 5;                     // warp within the group
     constexpr int W = Grp<G>::kWarps;
     int* cnt = mode == kGlobal ? gtab : slice;
-    const long long zero_n = mode == kLane ? C * G : mode == kWarp ? C * W : C;
+    const long long zero_n = mode == kLane ? C * G : mode == kLane16 ? (C + 1) / 2 * 32 : mode == kWarp ? C * W : C;
     for (long long k = r; k < zero_n; k += G) cnt[k] = 0;
     Grp<G>::sync();
     switch (mode) {
         case kLane: count_dispatch<G, kLane>(s, cnt + (long long)warp * C * 32 + lane); break;
+        case kLane16: count_dispatch<G, kLane16>(s, cnt + lane); break;
         case kWarp: count_dispatch<G, kWarp>(s, cnt + (long long)warp * C); break;
         default: count_dispatch<G, kShared>(s, cnt); break;
     }
     Grp<G>::sync();
     int* T;
-    if (mode == kLane) {
+    if (mode == kLane16) {   // one warp: lane l folds the 32 columns of cells l, l + 32, ...
+        T = slice + (C + 1) / 2 * 32;
+        for (long long c = lane; c < C; c += 32) {
+            const int* row = cnt + (c >> 1) * 32;
+            const int sh = (int)(c & 1) * 16;
+            int sum = 0;
+#pragma unroll 8
+            for (int l = 0; l < 32; ++l) sum += (row[(l + (int)c) & 31] >> sh) & 0xFFFF;
+            T[c] = sum;
+        }
+        *M = T + C;
+    } else if (mode == kLane) {
         // stage 1: each warp folds its 32 lane columns, lane l taking cells
         // c = l, l + 32, ...; the sum goes to column (c mod 32) of cell c's
         // row, which only that lane touches (and which keeps stage 2 free of

@@ -200,24 +200,24 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
     return before + x - v;
 }
 
-// One CTA per class.  Also picks the group size of the small-table class:
-// the smallest whose group count the edges still fill twice over (groups[k]
-// = groups available with size 32 << k), unless the caller forces one.
+// One CTA per class.  Also picks the group size of the small-table class
+// from a cost model of the depth: with W work items and g(G) groups of G
+// threads, the pool runs ceil(W / g(G)) rounds of one test each, a test
+// costing a fixed latency (claim, setup, merge, decision; ~kTestOverhead
+// cycles) plus the counting of N samples over G threads (~kCyclesPerSample
+// per sample and thread).  groups[k] = groups of size 32 << k; the caller
+// may force a size.
+constexpr double kTestOverhead = 10000.0;
+constexpr double kCyclesPerSample = 8.0;
+
 __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, DepthCounters* ctr,
                        unsigned long long* __restrict__ alive, unsigned long long* __restrict__ base,
-                       long long g32, long long g64, long long g128, int forced_group)
+                       long long g32, long long g64, long long g128, long long g256, double mean_n,
+                       int forced_group)
 {
     __shared__ unsigned long long sh[32];
     if (!ctr->active) return;
     const long long maxc = (long long)ctr->maxc[cls];
-    if (threadIdx.x == 0 && cls == 0) {
-        const long long E = (long long)ctr->n_edges[0];
-        int g = kTestThreads;
-        if (E >= 2 * g128) g = 128;
-        if (E >= 2 * g64) g = 64;
-        if (E >= 2 * g32) g = 32;
-        ctr->gsel = forced_group ? forced_group : g;
-    }
     if (ctr->n_edges[cls] == 0) return;
     const int T = blockDim.x;
     const long long len = maxc + 1;
@@ -246,8 +246,24 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, Dep
         run += alive[c];
     }
     if (fhi == len && flo < fhi) {
-        ctr->total_items[cls] = base[maxc];
+        const unsigned long long W = base[maxc];
+        ctr->total_items[cls] = W;
         ctr->next_item[cls] = 0;
+        if (cls == 0) {
+            const long long groups[4] = {g32, g64, g128, g256};
+            int best = kTestThreads;
+            double best_t = 1e300;
+            for (int k = 0; k < 4; ++k) {
+                const int G = 32 << k;
+                const double rounds = (double)((W + groups[k] - 1) / groups[k]);
+                const double t = rounds * (kTestOverhead + kCyclesPerSample * mean_n / G);
+                if (t < best_t) {
+                    best_t = t;
+                    best = G;
+                }
+            }
+            ctr->gsel = forced_group ? forced_group : best;
+        }
     }
 }
 
@@ -645,10 +661,11 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
 
 void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
                   unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
-                  unsigned long long* cursor, int32_t* sorted, const long long groups[3], int forced_group,
-                  int grid, cudaStream_t st)
+                  unsigned long long* cursor, int32_t* sorted, const long long groups[4], double mean_n,
+                  int forced_group, int grid, cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], forced_group);
+    k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], groups[3], mean_n,
+                               forced_group);
     k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, ctr, alive, cursor, sorted);
 }
 
