@@ -108,6 +108,11 @@ struct Workspace {
     long long gram_units_cap = 0;
     int gram_n_units = 0;
     std::vector<uint8_t> h_maps;
+    // CUDA graphs of one generic depth: [parity][big-table class queued]
+    cudaGraphExec_t graph[2][2] = {};
+    std::vector<uint8_t> graph_key;
+    cudaEvent_t gkev[2][2] = {};   // test-kernel window per parity
+    cudaEvent_t gdone[2] = {};     // loop flag copied, per parity
     bool events = false;
 
     void release()
@@ -123,6 +128,14 @@ struct Workspace {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
             for (auto& e : done) cudaEventDestroy(e);
+        }
+        for (auto& row : graph)
+            for (auto& g : row)
+                if (g) cudaGraphExecDestroy(g);
+        if (events) {
+            for (auto& row : gkev)
+                for (auto& e : row) cudaEventDestroy(e);
+            for (auto& e : gdone) cudaEventDestroy(e);
         }
         dfree(d_rec);
         if (h_rec) cudaFreeHost(h_rec);
@@ -219,6 +232,9 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         for (auto& e : ws.ev) CK(cudaEventCreate(&e));
         for (auto& e : ws.kev) CK(cudaEventCreate(&e));
         for (auto& e : ws.done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (auto& row : ws.gkev)
+            for (auto& e : row) CK(cudaEventCreate(&e));
+        for (auto& e : ws.gdone) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ws.events = true;
         CK(dalloc(&ws.d_rec, kMaxDepthRecords));
         CK(cudaMallocHost((void**)&ws.h_rec, kMaxDepthRecords * sizeof(DepthRecord)));
@@ -558,76 +574,146 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     base.crit = ct;
     base.alpha = alpha;
 
-    int queued = 0;
-    for (int d = 0; d < kMaxDepthRecords; ++d) {
-        if (max_depth >= 0 && d > max_depth) break;
-        CK(cudaEventRecord(ws.ev[d], st));
+    // The kernels of one depth after the edge list: ordering + pool per class,
+    // then removal and the end of the depth.
+    auto enqueue_tests = [&](bool big_possible) -> int {
+        for (int cls = 0; cls < 2; ++cls) {
+            if (cls == kClassCta && !big_possible) continue;
+            PoolArgs a = base;
+            a.cls = cls;
+            const bool small = cls == kClassWarp && !plain;
+            const size_t smem = small ? kWarpSmemBytes : kSmemBytes;
+            a.smem_ints = (int)(smem / 4);
+            if (!small && ws.gs_cells > 0) {
+                a.gscratch = ws.gscratch;
+                a.gscratch_ints = 3 * ws.gs_cells + 64;
+            }
+            if (plain) {
+                launch_plain(a, grid_big, kSmemBytes, st);
+                continue;
+            }
+            unsigned long long* cls_base = ws.base + cls * ws.ord_cap;
+            a.base = cls_base;
+            a.sorted = ws.sorted;
+            // the two classes share the sorted array: the next class's ordering
+            // runs after this pool on the same stream
+            launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap, ws.alive + cls * ws.ord_cap,
+                         cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups, mean_n, forced, grid_aux, st);
+            launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
+        }
+        return plain ? (big_possible ? 2 : 1) : (big_possible ? 6 : 3);
+    };
+    auto enqueue_head = [&]() {
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
         launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, gs_forced, gs_edges, ws.binom, ws.brows, wcap,
                      ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
-        launches += 2;
-        // the big-table class can only be non-empty once max_arity^(d+2) tops
-        // the small-table bound
+    };
+    // events inside a captured graph must be recorded as external event nodes
+    auto record = [&](cudaEvent_t ev, bool capturing) {
+        return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
+    };
+    auto enqueue_tail = [&](int* active_dst, cudaEvent_t done_ev, bool capturing) -> int {
+        launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
+                     grid_aux, st);
+        launch_depth_end(ws.d_ctr, ws.d_rec, max_depth, ws.hist, ws.cursor, st);
+        CK(cudaMemcpyAsync(active_dst, &ws.d_ctr->active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(record(done_ev, capturing));
+        return FBN_OK;
+    };
+    auto big_at = [&](int d) {   // the big-table class is possible once max_arity^(d+2) tops the bound
         long long bound = 1;
         for (int q = 0; q < d + 2 && bound <= wcap; ++q) bound *= max_ar;
-        const bool big_possible = bound > wcap;
-        CK(cudaEventRecord(ws.kev[2 * d], st));
+        return bound > wcap;
+    };
+
+    // Graphs of a generic depth, captured once per configuration: every
+    // argument they hold goes into the key.
+    {
+        std::vector<uint8_t> key;
+        auto put = [&](const void* p, size_t n) {
+            const uint8_t* b = (const uint8_t*)p;
+            key.insert(key.end(), b, b + n);
+        };
+        const void* ptrs[] = {ws.probs, ws.vtx_prob, ws.vtx_first, ws.binom, ws.edges, ws.min_accept, ws.d_ctr,
+                              ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.gscratch, ws.sep_pool, ws.d_rec,
+                              ws.h_active, ws.crit_keys, ws.crit_vals, (void*)st};
+        put(ptrs, sizeof ptrs);
+        const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
+                                  grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain, max_ar,
+                                  groups[0], groups[1], groups[2], groups[3]};
+        put(ints, sizeof ints);
+        put(&mean_n, sizeof mean_n);
+        put(&alpha, sizeof alpha);
+        if (key != ws.graph_key) {
+            for (auto& row : ws.graph)
+                for (auto& g : row)
+                    if (g) {
+                        cudaGraphExecDestroy(g);
+                        g = nullptr;
+                    }
+            for (int par = 0; par < 2; ++par)
+                for (int big = 0; big < 2; ++big) {
+                    cudaGraph_t graph = nullptr;
+                    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+                    enqueue_head();
+                    record(ws.gkev[par][0], true);
+                    enqueue_tests(big != 0);
+                    record(ws.gkev[par][1], true);
+                    enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], true);
+                    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+                    if (ce != cudaSuccess) return fail(h, FBN_ECUDA, "depth graph capture: %s", cudaGetErrorString(ce));
+                    const cudaError_t ie = cudaGraphInstantiate(&ws.graph[par][big], graph, 0);
+                    cudaGraphDestroy(graph);
+                    if (ie != cudaSuccess) return fail(h, FBN_ECUDA, "depth graph: %s", cudaGetErrorString(ie));
+                }
+            ws.graph_key = key;
+        }
+    }
+
+    fbn_stats stats{};
+    int queued = 0;
+    for (int d = 0; d < kMaxDepthRecords - 2; ++d) {
+        if (max_depth >= 0 && d > max_depth) break;
+        CK(cudaEventRecord(ws.ev[d], st));
+        const int par = d & 1;
         if (d == 0 && gram) {
+            enqueue_head();
+            CK(cudaEventRecord(ws.gkev[par][0], st));
             rc = run_gram(h, ws, k, total_vtx, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS],
                           ws.kev[2 * FBN_MAX_DEPTHS + 1]);
             if (rc) return rc;
             CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr, grid_aux, st));
-            launches += 4;
+            CK(cudaEventRecord(ws.gkev[par][1], st));
+            rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
+            if (rc) return rc;
+            launches += 8;
         } else {
-            for (int cls = 0; cls < 2; ++cls) {
-                if (cls == kClassCta && !big_possible) continue;
-                PoolArgs a = base;
-                a.cls = cls;
-                const bool small = cls == kClassWarp && !plain;
-                const size_t smem = small ? kWarpSmemBytes : kSmemBytes;
-                a.smem_ints = (int)(smem / 4);
-                if (!small && ws.gs_cells > 0) {
-                    a.gscratch = ws.gscratch;
-                    a.gscratch_ints = 3 * ws.gs_cells + 64;
-                }
-                if (plain) {
-                    launch_plain(a, grid_big, kSmemBytes, st);
-                    launches += 1;
-                    continue;
-                }
-                unsigned long long* cls_base = ws.base + cls * ws.ord_cap;
-                a.base = cls_base;
-                a.sorted = ws.sorted;
-                launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap,
-                             ws.alive + cls * ws.ord_cap, cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups,
-                             mean_n, forced, grid_aux, st);
-                launches += 2;
-                launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
-                launches += 1;
-                // the two classes share the sorted array: the next class's ordering
-                // runs after this pool on the same stream
-            }
+            const bool big = big_at(d);
+            CK(cudaGraphLaunch(ws.graph[par][big ? 1 : 0], st));
+            launches += 4 + (plain ? (big ? 2 : 1) : (big ? 6 : 3));
         }
         CK(cudaGetLastError());
-        CK(cudaEventRecord(ws.kev[2 * d + 1], st));
-        launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
-                     grid_aux, st);
-        launch_depth_end(ws.d_ctr, ws.d_rec, max_depth, ws.hist, ws.cursor, st);
-        launches += 2;
-        CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(&ws.h_active[d], &ws.d_ctr->active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaEventRecord(ws.done[d], st));
         queued = d + 1;
-        // depth d is queued; stop queueing once depth d-1 ended the loop
+        // depth d is queued; read depth d-1 (its slot is reused by depth d+1)
+        // and stop queueing once it ended the loop
         if (d >= 1) {
-            CK(cudaEventSynchronize(ws.done[d - 1]));
-            if (!ws.h_active[d - 1]) break;
+            const int pp = (d - 1) & 1;
+            CK(cudaEventSynchronize(ws.gdone[pp]));
+            float kms = 0.f;
+            CK(cudaEventElapsedTime(&kms, ws.gkev[pp][0], ws.gkev[pp][1]));
+            stats.test_ms[d - 1] = kms;
+            if (!ws.h_active[kMaxDepthRecords - 2 + pp]) break;
         }
     }
     CK(cudaEventRecord(ws.ev[queued], st));
     CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ws.h_rec, ws.d_rec, kMaxDepthRecords * sizeof(DepthRecord), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (queued > 0) {
+        float kms = 0.f;
+        CK(cudaEventElapsedTime(&kms, ws.gkev[(queued - 1) & 1][0], ws.gkev[(queued - 1) & 1][1]));
+        stats.test_ms[queued - 1] = kms;
+    }
     const DepthCounters& c = *ws.h_ctr;
     if (c.status & (kStatusSepPool | kStatusScratch)) {
         if (c.status & kStatusSepPool) {
@@ -646,20 +732,20 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     rc = check_status(h, c.status);
     if (rc) return rc;
 
-    fbn_stats stats{};
     for (int d = 0; d < queued; ++d) {
         const DepthRecord& r = ws.h_rec[d];
-        if (r.edges == 0) break;   // the depth that found no edge: Algorithm 1 stopped before it
+        if (r.edges == 0) {   // the depth that found no edge: Algorithm 1 stopped before it
+            stats.test_ms[d] = 0;
+            break;
+        }
         stats.depths = d + 1;
         stats.edges[d] = r.edges;
         stats.tests[d] = r.tests;
         stats.tests_oracle[d] = r.tests_oracle;
         stats.removed[d] = r.removed;
-        float ms = 0.f, kms = 0.f;
+        float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, ws.ev[d], ws.ev[d + 1]));
-        CK(cudaEventElapsedTime(&kms, ws.kev[2 * d], ws.kev[2 * d + 1]));
         stats.ms[d] = ms;
-        stats.test_ms[d] = kms;
     }
     if (gram && queued > 0) {
         float gms = 0.f;

@@ -413,12 +413,13 @@ __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 // packs two lane-private counters per word: a lane counts at most
 // N / 32 + 16 samples, which must stay below 2^16.  Its extra zeroing and
 // merge only pay off when the sample loop is long (measured: a gain at
-// N = 100,000, a loss at N around 12,500), hence N >= 32768.
+// N = 100,000, a loss for the batched problems of 1,000-50,000 samples),
+// hence N >= 65536.
 template <int G>
 __device__ __forceinline__ int pick_mode(long long C, long long marg, long long slice_ints, int N)
 {
     if (C * G + C + marg <= slice_ints) return kLane;
-    if (G == 32 && N >= 32768 && N / 32 + 32 < 65536 && (C + 1) / 2 * 32 + C + marg <= slice_ints) return kLane16;
+    if (G == 32 && N >= 65536 && N / 32 + 32 < 65536 && (C + 1) / 2 * 32 + C + marg <= slice_ints) return kLane16;
     if (Grp<G>::kWarps > 1 && C * Grp<G>::kWarps + marg <= slice_ints) return kWarp;
     if (C + marg <= slice_ints) return kShared;
     return kGlobal;
