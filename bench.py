@@ -100,6 +100,24 @@ def workload_config(name, w, args):
     return cfg
 
 
+# ----------------------------------------------------------------------------- ranks
+def rank_max(x, dist=None):
+    """Max of a float over the ranks (each rank runs an independent replica;
+    the job is as slow as its slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(tests_per_rank, ms_max, world):
+    """Whole-job tests per second: every rank's tests over the slowest rank's time."""
+    return world * tests_per_rank / (ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------- clocks
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -315,11 +333,8 @@ def main():
     ms = sum(step_ms) / len(step_ms)
     st = F.fbn_get_stats(handles[0])
     tests = sum(st["tests_oracle"])
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * tests / (ms / 1e3)
+    ms = rank_max(ms, dist)
+    value = job_throughput(tests, ms, world)
 
     # rooflines.  Histogram test kernels (the work pool): algorithmic sample
     # bytes (d + 2) N per oracle-equivalent test over their CUDA-event time,

@@ -48,7 +48,9 @@ typedef struct fbn_options {
     int32_t depth0;      /* FBN_DEPTH0_* */
     int32_t device;      /* CUDA device ordinal; -1 = the current device */
     int32_t group_threads; /* threads per CI test in the pool: 32, 64, 128 or 256; 0 = chosen per depth */
-    int32_t reserved[11];/* must be zero */
+    int32_t wait_limit;  /* attempts of each bounded device wait of the depth-0 Gram pipeline; 0 = default
+                            (2^22); -1 = give up at once, which exercises the FBN_ETIMEOUT path */
+    int32_t reserved[10];/* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */

@@ -445,7 +445,7 @@ int run_gram(fbn_handle* h, Workspace& ws, int k, int total_vtx, unsigned* d_sta
     CK(launch_onehot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st));
     CK(cudaMemsetAsync(ws.gram_G, 0, ws.gram_G_cap * sizeof(int32_t), st));
     if (ev0) CK(cudaEventRecord(ev0, st));
-    CK(launch_gram(ws.gram_maps, ws.gram_units, ws.gram_n_units, ws.probs, sms, d_status, st));
+    CK(launch_gram(ws.gram_maps, ws.gram_units, ws.gram_n_units, ws.probs, sms, d_status, h->opt.wait_limit, st));
     if (ev1) CK(cudaEventRecord(ev1, st));
     return FBN_OK;
 }
@@ -890,8 +890,9 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 11; ++k)
+        for (int k = 0; k < 10; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
+        if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
         if (o.group_threads != 0 && o.group_threads != 32 && o.group_threads != 64 && o.group_threads != 128 &&
             o.group_threads != kTestThreads)
             return fail(nullptr, FBN_EINVAL, "bad group_threads %d", o.group_threads);

@@ -86,9 +86,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 // Bounded wait for the completion of the phase with the given parity.  Gives
 // up (and raises the CTA's abort flag and the status bit) after kSpinLimit
 // attempts, or as soon as another role of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* status)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* status,
+                                          unsigned limit = kSpinLimit)
 {
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         if (mbar_try(bar, parity)) return true;
         if ((it & 255u) == 255u && *abort_flag) return false;
     }
@@ -159,6 +160,7 @@ struct GramArgs {
     const ProblemDev* probs;
     int n_units;
     unsigned* status;
+    unsigned limit;             // attempts of each role's bounded wait
 };
 
 __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
                 const int kb0 = t.w * kSlicesPerChunk;
                 const int kb1 = min(kb0 + kSlicesPerChunk, slices);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag, g.status)) break;
+                    if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag, g.status, g.limit)) break;
                     const uint32_t fb = smem_u32(&full[stage]);
                     const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
                     mbar_expect_tx(fb, kStageBytes);
@@ -248,11 +250,11 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
                 const int slices = (int)(g.probs[t.x].onehot_ld / kKSlice);
                 const int kb0 = t.w * kSlicesPerChunk;
                 const int kb1 = min(kb0 + kSlicesPerChunk, slices);
-                if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag, g.status)) break;
+                if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag, g.status, g.limit)) break;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * kTile);
                 for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag, g.status)) {
+                    if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag, g.status, g.limit)) {
                         ok = false;
                         break;
                     }
@@ -274,8 +276,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
                 if (acc == 0) acc_phase ^= 1u;
             }
             // every MMA this thread issued has finished before TMEM is released
+            // (the default bound here, whatever the roles' bound)
             mma_commit(smem_u32(drain));
-            mbar_wait(smem_u32(drain), 0, abort_flag, g.status);
+            for (unsigned it = 0; it < kSpinLimit; ++it)
+                if (mbar_try(smem_u32(drain), 0)) break;
         }
     } else {
         // ---------------- epilogue: warps 0-3, TMEM lanes 32w .. 32w+31
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
             const int4 t = g.units[u];
             int32_t* G = g.probs[t.x].gram;
             const long long ldg = g.probs[t.x].gram_ld;
-            if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag, g.status)) break;
+            if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag, g.status, g.limit)) break;
             tc_fence_after();
             const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kTile);
             const long long row0 = (long long)t.y * kTile + warp * 32;
@@ -567,7 +571,7 @@ int gram_chunks(long long K) { return (int)((K / kKSlice + kSlicesPerChunk - 1) 
 // problem's Gram must be zero.  maps: device array of tensor maps (one per
 // problem, 64-byte aligned).
 cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const ProblemDev* probs, int num_sms,
-                        unsigned* status, cudaStream_t st)
+                        unsigned* status, int wait_limit, cudaStream_t st)
 {
     GramArgs g;
     g.maps = reinterpret_cast<const CUtensorMap*>(maps);
@@ -575,6 +579,7 @@ cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const 
     g.probs = probs;
     g.n_units = n_units;
     g.status = status;
+    g.limit = wait_limit < 0 ? 0u : wait_limit == 0 ? kSpinLimit : (unsigned)wait_limit;
     cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGramSmem);
     if (e != cudaSuccess) return e;
     const int grid = n_units < num_sms ? n_units : num_sms;

@@ -19,7 +19,7 @@ cudaError_t encode_onehot_map(void* map, const uint8_t* E, int Mp, long long K);
 size_t tensor_map_bytes();
 int gram_chunks(long long K);
 cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const ProblemDev* probs, int num_sms,
-                        unsigned* status, cudaStream_t st);
+                        unsigned* status, int wait_limit, cudaStream_t st);
 cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs,
                                 unsigned long long* min_accept, const CritTableDev& crit, double alpha,
                                 DepthCounters* ctr, int grid, cudaStream_t st);

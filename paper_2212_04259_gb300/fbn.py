@@ -37,7 +37,8 @@ class FbnError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("form", C.c_int32), ("group_size", C.c_int32), ("depth0", C.c_int32),
-                ("device", C.c_int32), ("group_threads", C.c_int32), ("reserved", C.c_int32 * 11)]
+                ("device", C.c_int32), ("group_threads", C.c_int32), ("wait_limit", C.c_int32),
+                ("reserved", C.c_int32 * 10)]
 
 
 class Stats(C.Structure):
@@ -141,14 +142,14 @@ def _as_u8_2d(data):
 
 
 def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-1,
-               group_threads=0) -> Handle:
+               group_threads=0, wait_limit=0) -> Handle:
     """Upload variable-major uint8 data [n_vars][n_samples] (numpy, or torch host/device)."""
     data, (n, N) = _as_u8_2d(data)
     ar = np.ascontiguousarray(arities, dtype=np.uint8)
     if ar.shape != (n,):
         raise ValueError("arities must have one entry per variable")
     o = Options(form=FORMS[form], group_size=group_size, depth0=DEPTH0[depth0], device=device,
-                group_threads=group_threads)
+                group_threads=group_threads, wait_limit=wait_limit)
     out = C.c_void_p()
     rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
     _check(rc)

@@ -107,3 +107,18 @@ def test_batched_gram_skeletons_match_oracle(F):
         for i, j in [(0, 1), (2, len(a) - 1)]:
             blk = G[off[i]:off[i] + a[i], off[j]:off[j] + a[j]].ravel()
             assert np.array_equal(blk, oracle.ci_table(d, a, i, j))
+
+
+def test_gram_wait_timeout_is_reported_and_recoverable(F):
+    # every bounded wait of the Gram pipeline gives up at once: the kernel
+    # issues no copy, releases its tensor memory and reports FBN_ETIMEOUT;
+    # the context stays usable
+    data, ar, _ = bnsynth.make_dataset(77, 150, 180, 3, (2, 3, 4, 5), 1.0, 9000)
+    h = F.fbn_create(data, ar, depth0="gram", wait_limit=-1)
+    with pytest.raises(F.FbnError) as e:
+        F.fbn_learn_skeleton(h, 0.05, 0)
+    assert e.value.code == -6
+    h2 = F.fbn_create(data, ar, depth0="gram")
+    adj = F.fbn_learn_skeleton(h2, 0.05, 0)
+    ref = oracle.pc_stable(data, ar, 0.05, 0)
+    assert np.array_equal(adj, ref.adj)
