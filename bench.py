@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--form", choices=["pool", "plain"], default="pool")
     ap.add_argument("--gs", type=int, default=0)
     ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
+    ap.add_argument("--depth1", choices=["auto", "pool", "tensor"], default="auto",
+                    help="depth-1 counting: tensor-core neighbourhood product or work pool")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -278,12 +280,12 @@ def main():
     if w["kind"] == "single":
         data_dev = torch.from_numpy(w["data"]).cuda()
         handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local,
-                                group_threads=args.group_threads)]
+                                group_threads=args.group_threads, depth1=args.depth1)]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((w["data"].shape[0],) * 2, dtype=torch.uint8, device="cuda")]
     else:
         handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local,
-                                group_threads=args.group_threads)
+                                group_threads=args.group_threads, depth1=args.depth1)
                    for d, a in w["probs"]]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8, device="cuda") for d, _ in w["probs"]]
@@ -388,13 +390,13 @@ def main():
         host = torch.from_numpy(w["data"]).pin_memory()
         n = w["data"].shape[0]
         adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
-        he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local)
+        he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local, depth1=args.depth1)
         F.fbn_set_stream(he, stream)
         hs_e2e, hosts, adjs_host = [he], [host], [adj_host]
     else:
         hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
         adjs_host = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8).pin_memory() for d, _ in w["probs"]]
-        hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local)
+        hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local, depth1=args.depth1)
                   for hh, (_, a) in zip(hosts, w["probs"])]
         F.fbn_set_stream(hs_e2e[0], stream)
     e2e_ms, d2h = [], 0

@@ -42,6 +42,10 @@ extern "C" {
 #define FBN_DEPTH0_HIST 1  /* depth 0 through the shared-memory histogram path */
 #define FBN_DEPTH0_GRAM 2  /* depth 0 through the tcgen05 one-hot Gram */
 
+#define FBN_DEPTH1_AUTO   0  /* the work pool (the faster of the two on the measured workloads) */
+#define FBN_DEPTH1_POOL   1  /* depth 1 through the work pool */
+#define FBN_DEPTH1_TENSOR 2  /* depth 1 through the tcgen05 neighbourhood product (arities <= 8, else FBN_EINVAL) */
+
 typedef struct fbn_options {
     int32_t form;        /* FBN_FORM_POOL (default) or FBN_FORM_PLAIN */
     int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default (1) */
@@ -49,8 +53,11 @@ typedef struct fbn_options {
     int32_t device;      /* CUDA device ordinal; -1 = the current device */
     int32_t group_threads; /* threads per CI test in the pool: 32, 64, 128 or 256; 0 = chosen per depth */
     int32_t wait_limit;  /* attempts of each bounded device wait of the depth-0 Gram pipeline; 0 = default
-                            (2^22); -1 = give up at once, which exercises the FBN_ETIMEOUT path */
-    int32_t reserved[10];/* must be zero */
+                            (2^22); -1 = give up at once, which exercises the FBN_ETIMEOUT path (also the depth-1
+                            tensor-core pipeline) */
+    int32_t depth1;      /* FBN_DEPTH1_*: how depth 1 counts its tables (pool form only); every test of a
+                            vertex's neighbourhood at once on the tensor cores, or the work pool */
+    int32_t reserved[9]; /* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */

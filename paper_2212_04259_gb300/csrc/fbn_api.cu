@@ -13,6 +13,7 @@
 
 #include "../../include/fbn.h"
 #include "fbn_gram.h"
+#include "fbn_nbr.h"
 #include "fbn_launch.h"
 
 using namespace fbn;
@@ -106,6 +107,9 @@ struct Workspace {
     long long gram_maps_cap = 0;
     int4* gram_units = nullptr;
     long long gram_units_cap = 0;
+    // samples 4 bits each, problem after problem (depth 1 on the tensor cores)
+    uint8_t* pk = nullptr;
+    long long pk_cap = 0;
     int gram_n_units = 0;
     std::vector<uint8_t> h_maps;
     // CUDA graphs of one generic depth: [parity][big-table class queued]
@@ -123,7 +127,7 @@ struct Workspace {
         if (h_ctr) cudaFreeHost(h_ctr);
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
         dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals);
-        dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units);
+        dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
         if (events) {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
@@ -141,7 +145,7 @@ struct Workspace {
         if (h_rec) cudaFreeHost(h_rec);
         if (h_active) cudaFreeHost(h_active);
         h_maps.clear();
-        gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr;
+        gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr; pk = nullptr;
         *this = Workspace();
     }
 };
@@ -159,6 +163,7 @@ struct fbn_handle {
     uint8_t* d_ar = nullptr;
     uint8_t* d_adj = nullptr;
     int32_t* d_nbr = nullptr;
+    int32_t* d_eid = nullptr;
     int32_t* d_deg = nullptr;
     int32_t* d_sep_len = nullptr;
     int64_t* d_sep_off = nullptr;
@@ -368,6 +373,41 @@ bool use_gram(fbn_handle* const* hs, int k)
     return M >= 512 && Nmax >= 4096;
 }
 
+// Depth 1 on the tensor cores: pool form, asked for, every arity within the
+// kernel's bound.  The work pool stays the default: on the measured workloads
+// it is faster, its early exit running about a quarter of the tests the
+// neighbourhood product evaluates.
+bool use_nbr1(fbn_handle* const* hs, int k)
+{
+    const fbn_handle* h = hs[0];
+    if (h->opt.form == FBN_FORM_PLAIN || h->opt.depth1 != FBN_DEPTH1_TENSOR) return false;
+    for (int p = 0; p < k; ++p)
+        if (hs[p]->max_arity > nbr1_max_arity()) return false;
+    return true;
+}
+
+// Room for every problem's samples at 4 bits each; sets the problems' pk rows.
+int prepare_pack(fbn_handle* const* hs, int k, Workspace& ws, ProblemDev* P)
+{
+    fbn_handle* h = hs[0];
+    long long total = 0;
+    for (int p = 0; p < k; ++p) total += (long long)hs[p]->n * (hs[p]->ld / 2);
+    if (total > ws.pk_cap) {
+        dfree(ws.pk);
+        ws.pk = nullptr;
+        ws.pk_cap = 0;
+        CK(dalloc(&ws.pk, total));
+        ws.pk_cap = total;
+    }
+    long long off = 0;
+    for (int p = 0; p < k; ++p) {
+        P[p].pk = ws.pk + off;
+        P[p].pk_ld = hs[p]->ld / 2;
+        off += (long long)hs[p]->n * (hs[p]->ld / 2);
+    }
+    return FBN_OK;
+}
+
 // Lay out the one-hot matrices and Grams of every problem in the workspace,
 // set the problems' pointers, and upload one tensor map per problem and the
 // work units (problem, tile pair, chunk), problem-major.
@@ -507,7 +547,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         total_vtx += q->n;
         for (int v = 0; v < q->n; ++v) vtx_prob.push_back(p);
         ProblemDev& d = P[p];
-        d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.deg = q->d_deg;
+        d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.eid = q->d_eid; d.deg = q->d_deg;
         d.sep_len = q->d_sep_len; d.sep_off = q->d_sep_off; d.ld = q->ld; d.n = q->n; d.N = (int32_t)q->N;
         d.max_arity = q->max_arity; d.pad = 0;
     }
@@ -515,6 +555,11 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     if (rc) return rc;
     const bool plain = h->opt.form == FBN_FORM_PLAIN;
     const bool gram = !plain && use_gram(hs, k);
+    const bool nbr1 = use_nbr1(hs, k);
+    if (nbr1) {
+        rc = prepare_pack(hs, k, ws, P.data());
+        if (rc) return rc;
+    }
     if (gram) {
         rc = prepare_gram(hs, k, ws, P.data());
         if (rc) return rc;
@@ -529,6 +574,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     k_init_graph<<<total_vtx, 256, 0, st>>>(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx);
     CK(cudaGetLastError());
     long long launches = 1;
+    if (nbr1) {
+        CK(launch_pack4(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st));
+        launches += 1;
+    }
 
     int dev_sms = 0;
     CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
@@ -687,6 +736,15 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
             if (rc) return rc;
             launches += 8;
+        } else if (d == 1 && nbr1) {
+            enqueue_head();
+            CK(cudaEventRecord(ws.gkev[par][0], st));
+            CK(launch_nbr1(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.edges, ws.min_accept, ct, alpha, ws.d_ctr,
+                           dev_sms, h->opt.wait_limit, st));
+            CK(cudaEventRecord(ws.gkev[par][1], st));
+            rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
+            if (rc) return rc;
+            launches += 5;
         } else {
             const bool big = big_at(d);
             CK(cudaGraphLaunch(ws.graph[par][big ? 1 : 0], st));
@@ -855,7 +913,7 @@ void free_handle(fbn_handle* h)
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->ws.release();
-    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_deg);
+    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
     dfree(h->d_off);
@@ -890,7 +948,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 10; ++k)
+        for (int k = 0; k < 9; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
         if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
         if (o.group_threads != 0 && o.group_threads != 32 && o.group_threads != 64 && o.group_threads != 128 &&
@@ -899,12 +957,15 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         if (o.form != FBN_FORM_POOL && o.form != FBN_FORM_PLAIN) return fail(nullptr, FBN_EINVAL, "bad form %d", o.form);
         if (o.group_size < 0) return fail(nullptr, FBN_EINVAL, "bad group_size %d", o.group_size);
         if (o.depth0 < FBN_DEPTH0_AUTO || o.depth0 > FBN_DEPTH0_GRAM) return fail(nullptr, FBN_EINVAL, "bad depth0 %d", o.depth0);
+        if (o.depth1 < FBN_DEPTH1_AUTO || o.depth1 > FBN_DEPTH1_TENSOR) return fail(nullptr, FBN_EINVAL, "bad depth1 %d", o.depth1);
     }
     int max_ar = 0;
     for (int v = 0; v < n_vars; ++v) {
         if (arities[v] < 2) return fail(nullptr, FBN_EINVAL, "arity of variable %d is %d < 2", v, arities[v]);
         max_ar = std::max(max_ar, (int)arities[v]);
     }
+    if (o.depth1 == FBN_DEPTH1_TENSOR && max_ar > nbr1_max_arity())
+        return fail(nullptr, FBN_EINVAL, "depth1 tensor takes arities <= %d, not %d", nbr1_max_arity(), max_ar);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -947,6 +1008,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     CKC(dalloc(&h->d_ar, n_vars));
     CKC(dalloc(&h->d_adj, nn));
     CKC(dalloc(&h->d_nbr, nn));
+    CKC(dalloc(&h->d_eid, nn));
     CKC(dalloc(&h->d_deg, n_vars));
     CKC(dalloc(&h->d_sep_len, nn));
     CKC(dalloc(&h->d_sep_off, nn));
@@ -959,6 +1021,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     CKC(cudaMallocHost((void**)&h->h_status, sizeof(unsigned long long)));
     cudaStream_t st = h->stream;
     CKC(cudaMemsetAsync(h->d_data, 0, (size_t)n_vars * h->ld, st));
+    CKC(cudaMemsetAsync(h->d_eid, 0, nn * sizeof(int32_t), st));
     CKC(cudaMemcpy2DAsync(h->d_data, h->ld, data, n_samples, n_samples, n_vars, cudaMemcpyDefault, st));
     CKC(cudaMemcpyAsync(h->d_ar, arities, n_vars, cudaMemcpyHostToDevice, st));
     // values must lie below their arity: checked on the device
@@ -993,7 +1056,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         CKC(cudaMemcpy(h->d_off, off.data(), n_vars * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     ProblemDev P{};
-    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.deg = h->d_deg;
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = n_vars; P.N = (int32_t)n_samples;
     P.max_arity = max_ar;
     CKC(cudaMemcpyAsync(h->d_prob, &P, sizeof P, cudaMemcpyHostToDevice, st));
@@ -1117,7 +1180,7 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
     int rc = grow_workspace(h, ws, (long long)h->n * (h->n - 1) / 2, h->n, 1, h->n);
     if (rc) return rc;
     ProblemDev P{};
-    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.deg = h->d_deg;
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = h->n; P.N = (int32_t)h->N;
     P.max_arity = h->max_arity;
     rc = prepare_gram(hs, 1, ws, &P);

@@ -45,6 +45,9 @@ struct ProblemDev {
     int32_t* gram;         // [gram_ld][gram_ld] INT32 Gram (upper tile triangle)
     int64_t onehot_ld;     // padded samples (multiple of 128)
     int64_t gram_ld;       // padded rows Mp (multiple of 128)
+    int32_t* eid;          // [n][n] edge of the current depth at each snapshot slot nbr[v][t]
+    uint8_t* pk;           // [n][pk_ld] samples 4 bits each (depth-1 tensor-core path; arities <= 8)
+    int64_t pk_ld;         // ld / 2
 };
 
 // One edge i<j of the current depth with its rank space: ranks [0, cnt_i) are
@@ -81,6 +84,7 @@ struct DepthCounters {
     int need_cells;                     // largest table that missed the global scratch (persists)
     int gs;                             // ranks per chunk this depth (set by k_edges)
     unsigned long long adj_ends;        // sum of the snapshot degrees (twice the live edges)
+    unsigned long long nbr_claim;       // vertex claims of the depth-1 tensor-core kernel
 };
 
 // Per-depth record written by k_depth_end.

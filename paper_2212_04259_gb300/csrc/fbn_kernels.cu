@@ -141,6 +141,8 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
             w.cnt_i = cnt_i; w.total = total;
             edges[e] = w;
             min_accept[e] = (unsigned long long)total;
+            P.eid[(long long)i * P.n + t] = (int32_t)e;
+            P.eid[(long long)j * P.n + lo] = (int32_t)e;
             const unsigned long long ch = (unsigned long long)chunk_count(total, gs);
             mc[c] = ch > mc[c] ? ch : mc[c];
             mcell[c] = cells > mcell[c] ? cells : mcell[c];
@@ -571,6 +573,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
         ctr->tests = ctr->tests_oracle = ctr->removed = 0;
         ctr->gsel = 0;
         ctr->adj_ends = 0;
+        ctr->nbr_claim = 0;
         ctr->d = next;
         __threadfence();
         ctr->active = stop ? 0 : 1;

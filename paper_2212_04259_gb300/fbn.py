@@ -20,6 +20,7 @@ FBN_OK, FBN_EINVAL, FBN_EDATA, FBN_ENOMEM, FBN_ECUDA, FBN_ETOOBIG, FBN_ETIMEOUT,
     0, -1, -2, -3, -4, -5, -6, -7
 FORMS = {"pool": 0, "plain": 1}
 DEPTH0 = {"auto": 0, "hist": 1, "gram": 2}
+DEPTH1 = {"auto": 0, "pool": 1, "tensor": 2}
 MAX_DEPTHS = 64
 
 # Every symbol include/fbn.h declares.
@@ -38,7 +39,7 @@ class FbnError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("form", C.c_int32), ("group_size", C.c_int32), ("depth0", C.c_int32),
                 ("device", C.c_int32), ("group_threads", C.c_int32), ("wait_limit", C.c_int32),
-                ("reserved", C.c_int32 * 10)]
+                ("depth1", C.c_int32), ("reserved", C.c_int32 * 9)]
 
 
 class Stats(C.Structure):
@@ -142,14 +143,14 @@ def _as_u8_2d(data):
 
 
 def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-1,
-               group_threads=0, wait_limit=0) -> Handle:
+               group_threads=0, wait_limit=0, depth1="auto") -> Handle:
     """Upload variable-major uint8 data [n_vars][n_samples] (numpy, or torch host/device)."""
     data, (n, N) = _as_u8_2d(data)
     ar = np.ascontiguousarray(arities, dtype=np.uint8)
     if ar.shape != (n,):
         raise ValueError("arities must have one entry per variable")
     o = Options(form=FORMS[form], group_size=group_size, depth0=DEPTH0[depth0], device=device,
-                group_threads=group_threads, wait_limit=wait_limit)
+                group_threads=group_threads, wait_limit=wait_limit, depth1=DEPTH1[depth1])
     out = C.c_void_p()
     rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
     _check(rc)

@@ -66,6 +66,12 @@ def test_create_rejects_bad_arguments_before_touching_a_device(built):
     with pytest.raises(f.FbnError) as e:
         f.fbn_create(np.zeros((2, 10), np.uint8), [2, 1])    # arity < 2
     assert e.value.code == -1
+    with pytest.raises(f.FbnError) as e:                     # the depth-1 tensor path takes arities <= 8
+        f.fbn_create(np.zeros((2, 10), np.uint8), [2, 9], depth1="tensor")
+    assert e.value.code == -1 and "arities <= 8" in str(e.value)
+    with pytest.raises(f.FbnError) as e:
+        f.fbn_create(np.zeros((2, 10), np.uint8), [2, 2], depth0="gram", form="pool", group_threads=48)
+    assert e.value.code == -1
 
 
 def test_no_cpu_fallback_without_gpu(built):

@@ -112,10 +112,13 @@ def _skeleton(F, data, ar, alpha, md, **opt):
     return h, adj, F.fbn_export_sepsets(h), F.fbn_get_stats(h)
 
 
-@pytest.mark.parametrize("opt", [dict(form="pool", group_size=1), dict(form="pool", group_size=4),
+@pytest.mark.parametrize("opt", [dict(form="pool"), dict(form="pool", group_size=1),
+                                 dict(form="pool", group_size=4),
                                  dict(form="pool", group_size=9), dict(form="plain"),
-                                 dict(form="pool", group_threads=32), dict(form="pool", group_threads=64),
+                                 dict(form="pool", group_threads=32),
+                                 dict(form="pool", group_threads=64),
                                  dict(form="pool", group_threads=128, group_size=2),
+                                 dict(form="pool", depth1="tensor"),
                                  dict(form="pool", group_threads=256, group_size=3)])
 @pytest.mark.parametrize("name", ["small", "mid"])
 def test_skeleton_parity(F, name, opt):
