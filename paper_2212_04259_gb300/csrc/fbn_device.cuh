@@ -391,12 +391,87 @@ __device__ __forceinline__ void count_wide(const TestSpec& s, int* base)
     }
 }
 
+// Tables of at most 256 cells: every partial index of a sample fits one byte,
+// so the four samples of a 32-bit word advance together in its four bytes --
+// acc * r_k + row_k never carries out of a byte because the result stays below
+// the cells counted so far.  One IMAD per row and 4 samples, then one byte
+// extraction per sample.
+template <int MODE>
+__device__ __forceinline__ void bump_bytes(int* base, unsigned acc)
+{
+    bump<MODE>(base, __byte_perm(acc, 0u, 0x4440));
+    bump<MODE>(base, __byte_perm(acc, 0u, 0x4441));
+    bump<MODE>(base, __byte_perm(acc, 0u, 0x4442));
+    bump<MODE>(base, __byte_perm(acc, 0u, 0x4443));
+}
+
+template <int G, int NR, int MODE>
+__device__ __forceinline__ void count_bytes(const TestSpec& s, int* base)
+{
+    const int nvec = s.N >> 4;
+    const int t0 = Grp<G>::rank();
+    const uint4* r[NR];
+    unsigned rad[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        r[k] = reinterpret_cast<const uint4*>(s.rows[k]);
+        rad[k] = (unsigned)s.rad[k];
+    }
+    int v = t0;
+    for (; v + G < nvec; v += 2 * G) {
+        uint4 w0[NR], w1[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) {
+            w0[k] = __ldg(r[k] + v);
+            w1[k] = __ldg(r[k] + v + G);
+        }
+        uint4 a0 = w0[0], a1 = w1[0];
+#pragma unroll
+        for (int k = 1; k < NR; ++k) {
+            a0.x = a0.x * rad[k] + w0[k].x; a0.y = a0.y * rad[k] + w0[k].y;
+            a0.z = a0.z * rad[k] + w0[k].z; a0.w = a0.w * rad[k] + w0[k].w;
+            a1.x = a1.x * rad[k] + w1[k].x; a1.y = a1.y * rad[k] + w1[k].y;
+            a1.z = a1.z * rad[k] + w1[k].z; a1.w = a1.w * rad[k] + w1[k].w;
+        }
+        bump_bytes<MODE>(base, a0.x); bump_bytes<MODE>(base, a0.y);
+        bump_bytes<MODE>(base, a0.z); bump_bytes<MODE>(base, a0.w);
+        bump_bytes<MODE>(base, a1.x); bump_bytes<MODE>(base, a1.y);
+        bump_bytes<MODE>(base, a1.z); bump_bytes<MODE>(base, a1.w);
+    }
+    if (v < nvec) {
+        uint4 a = __ldg(r[0] + v);
+#pragma unroll
+        for (int k = 1; k < NR; ++k) {
+            const uint4 w = __ldg(r[k] + v);
+            a.x = a.x * rad[k] + w.x; a.y = a.y * rad[k] + w.y;
+            a.z = a.z * rad[k] + w.z; a.w = a.w * rad[k] + w.w;
+        }
+        bump_bytes<MODE>(base, a.x); bump_bytes<MODE>(base, a.y);
+        bump_bytes<MODE>(base, a.z); bump_bytes<MODE>(base, a.w);
+    }
+    for (int t = (nvec << 4) + t0; t < s.N; t += G) {
+        unsigned idx = s.rows[0][t];
+#pragma unroll
+        for (int k = 1; k < NR; ++k) idx = idx * rad[k] + s.rows[k][t];
+        bump<MODE>(base, idx);
+    }
+}
+
 template <int G, int MODE>
 __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 {
     if (s.cells > 65536) {
         count_wide<G, MODE>(s, base);
         return;
+    }
+    if (s.cells <= 256) {
+        switch (s.nrows) {
+            case 2: count_bytes<G, 2, MODE>(s, base); return;
+            case 3: count_bytes<G, 3, MODE>(s, base); return;
+            case 4: count_bytes<G, 4, MODE>(s, base); return;
+            case 5: count_bytes<G, 5, MODE>(s, base); return;
+            default: break;
+        }
     }
     switch (s.nrows) {
         case 2: count_packed<G, 2, MODE>(s, base); break;
