@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -150,6 +151,16 @@ struct Workspace {
     }
 };
 
+// A device array released when its last holder lets go.
+struct DeviceInts {
+    int32_t* d = nullptr;
+    long long n = 0;
+    ~DeviceInts()
+    {
+        if (d) cudaFree(d);
+    }
+};
+
 struct fbn_handle {
     int device = 0;
     cudaStream_t own_stream = nullptr;
@@ -188,6 +199,9 @@ struct fbn_handle {
     bool learnt = false;
     bool sep_pending = false;           // separating sets still only on the device
     unsigned long long sep_pool_used = 0;
+    // members of a batch's separating sets: a device copy of the batch's
+    // shared pool, held by every handle of that batch until it learns again
+    std::shared_ptr<DeviceInts> sep_snap;
     std::vector<int32_t> sep_len;      // n*n, i<j entries
     std::vector<int64_t> sep_off;      // n*n offsets into sep_members
     std::vector<int32_t> sep_members;
@@ -501,8 +515,9 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
     std::vector<int32_t> pool(h->sep_pool_used);
     std::vector<int32_t> len(nn);
     std::vector<int64_t> off(nn);
+    const int32_t* src = h->sep_snap ? h->sep_snap->d : ws.sep_pool;
     if (h->sep_pool_used)
-        CK(cudaMemcpyAsync(pool.data(), ws.sep_pool, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(pool.data(), src, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(len.data(), h->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(off.data(), h->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -815,17 +830,23 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         }
     }
     stats.launches = launches;
+    // every problem's sets stay on the device until asked for; a batch's
+    // members live in the first handle's pool, which its next call reuses, so
+    // the batch keeps a device copy of the used part
+    std::shared_ptr<DeviceInts> snap;
+    if (k > 1) {
+        snap = std::make_shared<DeviceInts>();
+        snap->n = std::max<long long>(1, (long long)c.sep_used);
+        CK(dalloc(&snap->d, snap->n));
+        if (c.sep_used)
+            CK(cudaMemcpyAsync(snap->d, ws.sep_pool, c.sep_used * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    }
     for (int p = 0; p < k; ++p) {
         hs[p]->stats = stats;
         hs[p]->learnt = true;
         hs[p]->sep_pending = true;
         hs[p]->sep_pool_used = c.sep_used;
-    }
-    if (k == 1) return FBN_OK;   // a single problem's sets stay on the device until asked for
-    // a batch shares the first handle's pool: bring every problem's sets over now
-    for (int p = 0; p < k; ++p) {
-        rc = materialize_sepsets(hs[p], ws);
-        if (rc) return rc;
+        hs[p]->sep_snap = snap;
     }
     return FBN_OK;
 }
