@@ -155,6 +155,8 @@ struct Workspace {
 struct DeviceInts {
     int32_t* d = nullptr;
     long long n = 0;
+    std::vector<int32_t> host;   // host copy, made by the first handle that asks
+    bool host_ready = false;
     ~DeviceInts()
     {
         if (d) cudaFree(d);
@@ -512,12 +514,29 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
     CK(cudaSetDevice(h->device));
     cudaStream_t st = h->stream;
     const size_t nn = (size_t)h->n * h->n;
-    std::vector<int32_t> pool(h->sep_pool_used);
+    // the members: this handle's own pool, or the batch's snapshot, copied
+    // to the host once for the whole batch
+    std::vector<int32_t> own;
+    const int32_t* pool = nullptr;
+    DeviceInts* snap = h->sep_snap.get();
+    if (snap) {
+        if (!snap->host_ready) {
+            snap->host.resize(h->sep_pool_used);
+            if (h->sep_pool_used)
+                CK(cudaMemcpyAsync(snap->host.data(), snap->d, h->sep_pool_used * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, st));
+            snap->host_ready = true;
+        }
+        pool = snap->host.data();
+    } else {
+        own.resize(h->sep_pool_used);
+        if (h->sep_pool_used)
+            CK(cudaMemcpyAsync(own.data(), ws.sep_pool, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                               st));
+        pool = own.data();
+    }
     std::vector<int32_t> len(nn);
     std::vector<int64_t> off(nn);
-    const int32_t* src = h->sep_snap ? h->sep_snap->d : ws.sep_pool;
-    if (h->sep_pool_used)
-        CK(cudaMemcpyAsync(pool.data(), src, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(len.data(), h->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(off.data(), h->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
