@@ -111,6 +111,13 @@ struct Workspace {
     // samples 4 bits each, problem after problem (depth 1 on the tensor cores)
     uint8_t* pk = nullptr;
     long long pk_cap = 0;
+    // launch geometry of the device, fixed once (kernel attributes set)
+    int dev_sms = 0, grid_small = 0, grid_big = 0;
+    // the problem descriptors and vertex maps as last uploaded (skipped when
+    // unchanged), staged through pinned memory
+    std::vector<uint8_t> up_last;
+    uint8_t* h_up = nullptr;
+    size_t h_up_cap = 0;
     int gram_n_units = 0;
     std::vector<uint8_t> h_maps;
     // CUDA graphs of one generic depth: [parity][big-table class queued]
@@ -145,6 +152,7 @@ struct Workspace {
         dfree(d_rec);
         if (h_rec) cudaFreeHost(h_rec);
         if (h_active) cudaFreeHost(h_active);
+        if (h_up) cudaFreeHost(h_up);
         h_maps.clear();
         gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr; pk = nullptr;
         *this = Workspace();
@@ -562,7 +570,8 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
 // and only waits for the loop flag of depth d-1.  *retry is set when a
 // separating-set pool or global-table scratch turned out too small (both are
 // grown before returning).
-int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, bool* retry)
+int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, bool* retry,
+                      uint8_t* const* adj_out)
 {
     fbn_handle* h = hs[0];
     Workspace& ws = h->ws;
@@ -602,9 +611,31 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         rc = ensure_sep_pool(h, ws, 2 * edge_cap + 1024, 0, st);
         if (rc) return rc;
     }
-    CK(cudaMemcpyAsync(ws.probs, P.data(), k * sizeof(ProblemDev), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ws.vtx_prob, vtx_prob.data(), total_vtx * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ws.vtx_first, vtx_first.data(), k * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    {   // problem descriptors and vertex maps: uploaded only when they changed
+        const size_t b0 = k * sizeof(ProblemDev), b1 = total_vtx * sizeof(int32_t), b2 = k * sizeof(int32_t);
+        const void* dst[3] = {ws.probs, ws.vtx_prob, ws.vtx_first};
+        std::vector<uint8_t> blob(sizeof dst + b0 + b1 + b2);
+        std::memcpy(blob.data(), dst, sizeof dst);
+        std::memcpy(blob.data() + sizeof dst, P.data(), b0);
+        std::memcpy(blob.data() + sizeof dst + b0, vtx_prob.data(), b1);
+        std::memcpy(blob.data() + sizeof dst + b0 + b1, vtx_first.data(), b2);
+        if (blob != ws.up_last) {
+            if (blob.size() > ws.h_up_cap) {
+                if (ws.h_up) cudaFreeHost(ws.h_up);
+                ws.h_up = nullptr;
+                ws.h_up_cap = 0;
+                CK(cudaMallocHost((void**)&ws.h_up, blob.size()));
+                ws.h_up_cap = blob.size();
+            }
+            // the staging buffer is free: every call ends with its stream drained
+            std::memcpy(ws.h_up, blob.data(), blob.size());
+            const uint8_t* src = ws.h_up + sizeof dst;
+            CK(cudaMemcpyAsync(ws.probs, src, b0, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(ws.vtx_prob, src + b0, b1, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(ws.vtx_first, src + b0 + b1, b2, cudaMemcpyHostToDevice, st));
+            ws.up_last.swap(blob);
+        }
+    }
     k_init_graph<<<total_vtx, 256, 0, st>>>(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx);
     CK(cudaGetLastError());
     long long launches = 1;
@@ -613,12 +644,16 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         launches += 1;
     }
 
-    int dev_sms = 0;
-    CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
-    CK(set_kernel_smem(kSmemBytes));
-    // CTAs of the small-table pool (any group size) and of the big-table pool
-    const int grid_small = dev_sms * std::max(1, pool_blocks_per_sm(kClassWarp, kWarpSmemBytes));
-    const int grid_big = dev_sms * std::max(1, pool_blocks_per_sm(kClassCta, kSmemBytes));
+    if (!ws.dev_sms) {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        CK(set_kernel_smem(kSmemBytes));
+        // CTAs of the small-table pool (any group size) and of the big-table pool
+        ws.grid_small = sms * std::max(1, pool_blocks_per_sm(kClassWarp, kWarpSmemBytes));
+        ws.grid_big = sms * std::max(1, pool_blocks_per_sm(kClassCta, kSmemBytes));
+        ws.dev_sms = sms;
+    }
+    const int dev_sms = ws.dev_sms, grid_small = ws.grid_small, grid_big = ws.grid_big;
     const long long groups[4] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2,
                                  (long long)grid_small};
     double mean_n = 0;
@@ -800,6 +835,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     CK(cudaEventRecord(ws.ev[queued], st));
     CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ws.h_rec, ws.d_rec, kMaxDepthRecords * sizeof(DepthRecord), cudaMemcpyDeviceToHost, st));
+    if (adj_out)   // the adjacency goes out with the counters (dropped if the call is retried)
+        for (int p = 0; p < k; ++p)
+            if (adj_out[p])
+                CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, (size_t)hs[p]->n * hs[p]->n, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
     if (queued > 0) {
         float kms = 0.f;
@@ -870,23 +909,14 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     return FBN_OK;
 }
 
-int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, uint8_t* const* adj_out = nullptr)
 {
     for (int attempt = 0; attempt < 6; ++attempt) {
         bool retry = false;
-        const int rc = run_skeleton_once(hs, k, alpha, max_depth, &retry);
+        const int rc = run_skeleton_once(hs, k, alpha, max_depth, &retry, adj_out);
         if (rc || !retry) return rc;
     }
     return fail(hs[0], FBN_ENOMEM, "scratch or separating-set pool kept overflowing");
-}
-
-int copy_adj(fbn_handle* h, uint8_t* adj_out)
-{
-    if (!adj_out) return FBN_OK;
-    const size_t nn = (size_t)h->n * h->n;
-    CK(cudaMemcpyAsync(adj_out, h->d_adj, nn, cudaMemcpyDefault, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    return FBN_OK;
 }
 
 int check_test_args(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, long long* cells)
@@ -1178,9 +1208,8 @@ int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* 
     if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
     h->learnt = false;
     fbn_handle* hs[1] = {h};
-    int rc = run_skeleton(hs, 1, alpha, max_depth);
-    if (rc) return rc;
-    return copy_adj(h, adj_out);
+    uint8_t* outs[1] = {adj_out};
+    return run_skeleton(hs, 1, alpha, max_depth, outs);
 }
 
 int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth,
@@ -1196,16 +1225,7 @@ int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int
     }
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
     if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
-    int rc = run_skeleton(hs, k, alpha, max_depth);
-    if (rc) return rc;
-    if (adj_out)
-        for (int p = 0; p < k; ++p) {
-            if (!adj_out[p]) continue;
-            const size_t nn = (size_t)hs[p]->n * hs[p]->n;
-            CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, nn, cudaMemcpyDefault, h->stream));
-        }
-    CK(cudaStreamSynchronize(h->stream));
-    return FBN_OK;
+    return run_skeleton(hs, k, alpha, max_depth, adj_out);
 }
 
 int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
@@ -1226,6 +1246,7 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
     rc = prepare_gram(hs, 1, ws, &P);
     if (rc) return rc;
     std::vector<int32_t> vp(h->n, 0), vf(1, 0);
+    ws.up_last.clear();   // the skeleton's next call uploads its own descriptors again
     CK(cudaMemcpyAsync(ws.probs, &P, sizeof P, cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(ws.vtx_prob, vp.data(), h->n * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     CK(cudaMemcpyAsync(ws.vtx_first, vf.data(), sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));

@@ -314,6 +314,13 @@ __device__ __forceinline__ void count_packed(const TestSpec& s, int* base)
                 w0[k] = __ldg(r[k] + v);
                 w1[k] = __ldg(r[k] + v + G);
             }
+            if (v + 3 * G < nvec) {   // the next iteration's lines into L1 while these are counted
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(r[k] + v + 2 * G));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(r[k] + v + 3 * G));
+                }
+            }
             unsigned acc[8];
             pack_vector<NR>(s, w0, acc);
             bump_packed<MODE>(base, acc);
@@ -424,6 +431,13 @@ __device__ __forceinline__ void count_bytes(const TestSpec& s, int* base)
         for (int k = 0; k < NR; ++k) {
             w0[k] = __ldg(r[k] + v);
             w1[k] = __ldg(r[k] + v + G);
+        }
+        if (v + 3 * G < nvec) {   // the next iteration's lines into L1 while these are counted
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(r[k] + v + 2 * G));
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(r[k] + v + 3 * G));
+            }
         }
         uint4 a0 = w0[0], a1 = w1[0];
 #pragma unroll
