@@ -24,6 +24,7 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr size_t kSmemBytes = 108 * 1024;     // dynamic shared memory of a CTA test group (2 CTAs / SM)
+constexpr long long kSplitStride = 4096;        // cells of a split test's global table at most
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
 
@@ -111,6 +112,11 @@ struct Workspace {
     // samples 4 bits each, problem after problem (depth 1 on the tensor cores)
     uint8_t* pk = nullptr;
     long long pk_cap = 0;
+    // global tables of tests split by samples; zero between uses (cleared
+    // again when a call did not run to its end)
+    int* split_tab = nullptr;
+    unsigned* split_ticket = nullptr;
+    bool split_dirty = false;
     // launch geometry of the device, fixed once (kernel attributes set)
     int dev_sms = 0, grid_small = 0, grid_big = 0;
     // the problem descriptors and vertex maps as last uploaded (skipped when
@@ -136,6 +142,7 @@ struct Workspace {
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
         dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals);
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
+        dfree(split_tab); dfree(split_ticket);
         if (events) {
             for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
@@ -155,6 +162,7 @@ struct Workspace {
         if (h_up) cudaFreeHost(h_up);
         h_maps.clear();
         gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr; pk = nullptr;
+        split_tab = nullptr; split_ticket = nullptr;
         *this = Workspace();
     }
 };
@@ -272,6 +280,9 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         if (orc) return orc;
         CK(dalloc(&ws.crit_keys, kCritCap));
         CK(dalloc(&ws.crit_vals, kCritCap));
+        CK(dalloc(&ws.split_tab, kSplitItems * kSplitStride));
+        CK(dalloc(&ws.split_ticket, kSplitItems));
+        ws.split_dirty = true;
     }
     if (edge_cap > ws.edge_cap) {
         dfree(ws.edges); dfree(ws.min_accept); dfree(ws.sorted);
@@ -656,6 +667,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     const int dev_sms = ws.dev_sms, grid_small = ws.grid_small, grid_big = ws.grid_big;
     const long long groups[4] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2,
                                  (long long)grid_small};
+    const long long groups_big[4] = {(long long)grid_big * 8, (long long)grid_big * 4, (long long)grid_big * 2,
+                                     (long long)grid_big};
     double mean_n = 0;
     for (int p = 0; p < k; ++p) mean_n += (double)hs[p]->N / k;
     int max_ar = 2;
@@ -691,6 +704,14 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     base.binom_rows = ws.brows;
     base.crit = ct;
     base.alpha = alpha;
+    base.split_tab = ws.split_tab;
+    base.split_ticket = ws.split_ticket;
+    base.split_stride = kSplitStride;
+    if (ws.split_dirty) {
+        CK(cudaMemsetAsync(ws.split_tab, 0, kSplitItems * kSplitStride * sizeof(int), st));
+        CK(cudaMemsetAsync(ws.split_ticket, 0, kSplitItems * sizeof(unsigned), st));
+    }
+    ws.split_dirty = true;   // until this call completes its loop
 
     // The kernels of one depth after the edge list: ordering + pool per class,
     // then removal and the end of the depth.
@@ -716,7 +737,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             // the two classes share the sorted array: the next class's ordering
             // runs after this pool on the same stream
             launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap, ws.alive + cls * ws.ord_cap,
-                         cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, groups, mean_n, forced, grid_aux, st);
+                         cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, small ? groups : groups_big, mean_n,
+                         forced, (long long)(smem / 4), kSplitStride, 1, grid_aux, st);
             launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
         }
         return plain ? (big_possible ? 2 : 1) : (big_possible ? 6 : 3);
@@ -754,7 +776,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         };
         const void* ptrs[] = {ws.probs, ws.vtx_prob, ws.vtx_first, ws.binom, ws.edges, ws.min_accept, ws.d_ctr,
                               ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.gscratch, ws.sep_pool, ws.d_rec,
-                              ws.h_active, ws.crit_keys, ws.crit_vals, (void*)st};
+                              ws.h_active, ws.crit_keys, ws.crit_vals, ws.split_tab, ws.split_ticket, (void*)st};
         put(ptrs, sizeof ptrs);
         const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
                                   grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain, max_ar,
@@ -846,6 +868,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         stats.test_ms[queued - 1] = kms;
     }
     const DepthCounters& c = *ws.h_ctr;
+    if (c.status == 0) ws.split_dirty = false;   // every split test's last part zeroed its table
     if (c.status & (kStatusSepPool | kStatusScratch)) {
         if (c.status & kStatusSepPool) {
             rc = ensure_sep_pool(h, ws, 2 * ws.sep_cap + 2 * (long long)c.sep_used, 0, st);

@@ -85,7 +85,17 @@ struct DepthCounters {
     int gs;                             // ranks per chunk this depth (set by k_edges)
     unsigned long long adj_ends;        // sum of the snapshot degrees (twice the live edges)
     unsigned long long nbr_claim;       // vertex claims of the depth-1 tensor-core kernel
+    unsigned long long max_total[2];    // largest rank count of an edge per class
+    int split[2];                       // sample parts per test per class (1 = whole tests)
 };
+
+// Tests split by samples: when a depth has few tests against the groups, every
+// test is counted by `split` groups over disjoint sample ranges; each part adds
+// its table into a zero global table of the test, and the part that finishes
+// last decides and zeroes the table again.
+constexpr int kMaxSplit = 16;
+constexpr long long kSplitMinSamples = 4096;   // samples per part at least
+constexpr long long kSplitItems = 4096;        // tests split at once at most
 
 // Per-depth record written by k_depth_end.
 constexpr int kMaxDepthRecords = 64;
@@ -136,6 +146,9 @@ struct PoolArgs {
     int32_t smem_ints;
     int32_t binom_rows;
     double alpha;
+    int* split_tab;                   // [kSplitItems][split_stride] zero global tables of split tests
+    unsigned* split_ticket;           // [kSplitItems] parts finished per test, zero between uses
+    long long split_stride;           // ints per split table
 };
 
 }  // namespace fbn

@@ -85,7 +85,7 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
     const int i = g - vtx_first[p];
     const int deg_i = P.deg[i];
     const int32_t* nb = P.nbr + (long long)i * P.n;
-    unsigned long long mc[2] = {0, 0}, mcell[2] = {0, 0};
+    unsigned long long mc[2] = {0, 0}, mcell[2] = {0, 0}, mtot[2] = {0, 0};
     for (int t0 = 0; t0 < deg_i; t0 += 32) {
         const int t = t0 + lane;
         int j = -1;
@@ -146,6 +146,7 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
             const unsigned long long ch = (unsigned long long)chunk_count(total, gs);
             mc[c] = ch > mc[c] ? ch : mc[c];
             mcell[c] = cells > mcell[c] ? cells : mcell[c];
+            mtot[c] = (unsigned long long)total > mtot[c] ? (unsigned long long)total : mtot[c];
         }
     }
 #pragma unroll
@@ -154,12 +155,15 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long a = __shfl_down_sync(0xffffffffu, mc[c], o);
             const unsigned long long b = __shfl_down_sync(0xffffffffu, mcell[c], o);
+            const unsigned long long t = __shfl_down_sync(0xffffffffu, mtot[c], o);
             mc[c] = a > mc[c] ? a : mc[c];
             mcell[c] = b > mcell[c] ? b : mcell[c];
+            mtot[c] = t > mtot[c] ? t : mtot[c];
         }
         if (lane == 0) {
             if (mc[c]) atomicMax(&ctr->maxc[c], mc[c]);
             if (mcell[c]) atomicMax(&ctr->max_cells[c], mcell[c]);
+            if (mtot[c]) atomicMax(&ctr->max_total[c], mtot[c]);
         }
     }
 }
@@ -215,7 +219,7 @@ constexpr double kCyclesPerSample = 8.0;
 __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, DepthCounters* ctr,
                        unsigned long long* __restrict__ alive, unsigned long long* __restrict__ base,
                        long long g32, long long g64, long long g128, long long g256, double mean_n,
-                       int forced_group)
+                       int forced_group, long long smem_ints, long long split_stride, int allow_split)
 {
     __shared__ unsigned long long sh[32];
     if (!ctr->active) return;
@@ -266,6 +270,23 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, Dep
             }
             ctr->gsel = forced_group ? forced_group : best;
         }
+        // sample split: few single-rank tests against the groups of the class
+        const int G = cls == 0 ? ctr->gsel : kTestThreads;
+        const long long groups = cls == 0 ? (G == 32 ? g32 : G == 64 ? g64 : G == 128 ? g128 : g256) : g256;
+        const long long slice = smem_ints * G / kTestThreads;
+        const long long mcell = (long long)ctr->max_cells[cls];
+        long long sp = 1;
+        if (allow_split && ctr->gs == 1 && ctr->max_total[cls] <= (unsigned long long)kMaxPasses &&
+            (long long)W * 2 <= groups && (long long)W <= kSplitItems && mcell <= split_stride &&
+                    (mcell * 9) / 4 + 64 <= slice) {
+            sp = groups / (long long)W;
+            const long long by_n = (long long)mean_n / kSplitMinSamples;
+            sp = sp < by_n ? sp : by_n;
+            sp = sp < kMaxSplit ? sp : kMaxSplit;
+            sp = sp > 1 ? sp : 1;
+        }
+        ctr->split[cls] = (int)sp;
+        ctr->total_items[cls] = W * (unsigned long long)sp;
     }
 }
 
@@ -289,6 +310,9 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, 
 struct GroupState {
     long long r0, r1;
     unsigned long long tests;
+    unsigned long long item;   // split tests: the test's item and this group's part
+    int part;
+    unsigned ticket;
     int e;
     int go;
     double crit;
@@ -370,6 +394,72 @@ __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemD
     return grp_decide<G>(spec, T, M, S.crit, red) ? 1 : 0;
 }
 
+// One part of a split test: count samples [N p / S, N (p + 1) / S) (16-aligned
+// bounds) of rank rk into the test's global table; the part that finishes last
+// copies the table into shared memory (L2 reads), zeroes it, decides and
+// lowers the edge's rank.  Returns 1 when this group decided an acceptance.
+template <int G>
+__device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w,
+                                              long long rk, int split, GroupState& S, TestSpec& spec, int* slice,
+                                              long long slice_ints, int* gtab, double* red,
+                                              const unsigned long long* min_accept_e)
+{
+    unsigned* status = &a.ctr->status;
+    const int r = Grp<G>::rank();
+    int* Tg = a.split_tab + (long long)S.item * a.split_stride;
+    if (r == 0) S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
+    Grp<G>::sync();
+    if (S.go && setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) {
+        const long long N = P.N;
+        const long long lo = (N * S.part / split) & ~15LL;
+        const long long hi = S.part == split - 1 ? N : ((N * (S.part + 1) / split) & ~15LL);
+        if (r < d + 2) spec.rows[r] += lo;
+        Grp<G>::sync();
+        if (r == 0) spec.N = (int)(hi - lo);
+        Grp<G>::sync();
+        int* M = nullptr;
+        const int* T = grp_table<G>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
+        if (!T) {
+            if (r == 0) {
+                atomicOr(status, kStatusScratch);
+                atomicMax(&a.ctr->need_cells, (int)spec.cells);
+            }
+        } else {
+            for (long long c = r; c < spec.cells; c += G)
+                if (T[c]) atomicAdd(Tg + c, T[c]);
+        }
+    }
+    __threadfence();
+    Grp<G>::sync();
+    if (r == 0) S.ticket = atomicAdd(&a.split_ticket[S.item], 1u);
+    Grp<G>::sync();
+    if (S.ticket != (unsigned)(split - 1)) return 0;
+    // the last part: every other part's adds are in L2
+    __threadfence();
+    if (!setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
+    const long long C = spec.cells;
+    int* Tl = slice;
+    for (long long c = r; c < C; c += G) {
+        Tl[c] = __ldcg(Tg + c);
+        Tg[c] = 0;
+    }
+    if (r == 0) {
+        a.split_ticket[S.item] = 0;
+        S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
+    }
+    Grp<G>::sync();
+    if (!S.go) return 0;
+    int* M = Tl + C;
+    grp_marginals<G>(spec, Tl, M);
+    if (r == 0) {
+        const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (C / (spec.rx * spec.ry));
+        S.crit = crit_get(a.crit, df, a.alpha, status);
+        S.tests += 1;
+    }
+    Grp<G>::sync();
+    return grp_decide<G>(spec, Tl, M, S.crit, red) ? 1 : 0;
+}
+
 // Shared state of a pool CTA, sized for the most groups per CTA (8 warps).
 struct PoolShared {
     TestSpec spec[kTestThreads / 32];
@@ -405,12 +495,16 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     GroupState& S = sh.st[g];
     TestSpec& spec = sh.spec[g];
     if (r == 0) S.tests = 0;
+    const int split = ctr->split[a.cls] > 1 ? ctr->split[a.cls] : 1;
 
     for (;;) {
         if (r == 0) {
-            const unsigned long long w = atomicAdd(next_item, 1ULL);
+            const unsigned long long wi = atomicAdd(next_item, 1ULL);
+            const unsigned long long w = wi / (unsigned long long)split;
+            S.item = w;
+            S.part = (int)(wi - w * (unsigned long long)split);
             S.e = -1;
-            if (w < total) {
+            if (wi < total) {
                 long long lo = 0, hi = maxc - 1;   // pass k: largest k with base[k] <= w
                 while (lo < hi) {
                     const long long mid = (lo + hi + 1) >> 1;
@@ -431,6 +525,13 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
         const EdgeWork w = edges[e];
         const ProblemDev& P = a.probs[w.prob];
         const long long r0 = S.r0, r1 = S.r1;
+        if (split > 1) {   // single-rank items (gs = 1, no edge above kMaxPasses ranks)
+            const int res = run_split_part<G>(a, d, P, w, r0, split, S, spec, slice, slice_ints, gtab, sh.red,
+                                              &min_accept[e]);
+            if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)r0);
+            Grp<G>::sync();
+            continue;
+        }
         for (long long rk = r0; rk < r1; ++rk) {
             if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&min_accept[e]);
             Grp<G>::sync();
@@ -574,6 +675,8 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
         ctr->gsel = 0;
         ctr->adj_ends = 0;
         ctr->nbr_claim = 0;
+        ctr->max_total[0] = ctr->max_total[1] = 0;
+        ctr->split[0] = ctr->split[1] = 1;
         ctr->d = next;
         __threadfence();
         ctr->active = stop ? 0 : 1;
@@ -665,10 +768,11 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
 void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
                   unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
                   unsigned long long* cursor, int32_t* sorted, const long long groups[4], double mean_n,
-                  int forced_group, int grid, cudaStream_t st)
+                  int forced_group, long long smem_ints, long long split_stride, int allow_split, int grid,
+                  cudaStream_t st)
 {
     k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], groups[3], mean_n,
-                               forced_group);
+                               forced_group, smem_ints, split_stride, allow_split);
     k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, ctr, alive, cursor, sorted);
 }
 

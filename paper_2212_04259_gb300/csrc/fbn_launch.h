@@ -25,7 +25,8 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
 void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
                   unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
                   unsigned long long* cursor, int32_t* sorted, const long long groups[4], double mean_n,
-                  int forced_group, int grid, cudaStream_t st);
+                  int forced_group, long long smem_ints, long long split_stride, int allow_split, int grid,
+                  cudaStream_t st);
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
