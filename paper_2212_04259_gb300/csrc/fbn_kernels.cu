@@ -32,10 +32,21 @@
 
 namespace fbn {
 
+// Programmatic dependent launch: the kernels of a depth are launched so that
+// the next one may be scheduled once every CTA of this one has started; it
+// then waits here until this one has finished and its writes are visible.
+// Launched without the attribute, both instructions do nothing.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
 __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
                            const int32_t* __restrict__ vtx_first, int total_vertices, DepthCounters* ctr)
 {
+    pdl_enter();
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= total_vertices || !ctr->active) return;
@@ -72,6 +83,7 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
                         EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
                         long long edge_cap, DepthCounters* ctr, unsigned long long* __restrict__ hist)
 {
+    pdl_enter();
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= total_vertices || !ctr->active) return;
@@ -221,6 +233,7 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, Dep
                        long long g32, long long g64, long long g128, long long g256, double mean_n,
                        int forced_group, long long smem_ints, long long split_stride, int allow_split)
 {
+    pdl_enter();
     __shared__ unsigned long long sh[32];
     if (!ctr->active) return;
     const long long maxc = (long long)ctr->maxc[cls];
@@ -294,6 +307,7 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, 
                         const DepthCounters* ctr, const unsigned long long* __restrict__ alive,
                         unsigned long long* __restrict__ cursor, int32_t* __restrict__ sorted)
 {
+    pdl_enter();
     if (!ctr->active) return;
     const int gs = ctr->gs;
     const long long E = (long long)ctr->n_edges[cls];
@@ -548,6 +562,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
 // Small-table class: the group size k_scan chose for this depth.
 __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
 {
+    pdl_enter();
     extern __shared__ int smem[];
     __shared__ PoolShared sh;
     if (!a.ctr->active) return;
@@ -562,6 +577,7 @@ __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
 // Big-table class: CTA groups.
 __global__ void __launch_bounds__(kTestThreads, 2) k_pool_big(PoolArgs a)
 {
+    pdl_enter();
     extern __shared__ int smem[];
     __shared__ PoolShared sh;
     if (!a.ctr->active) return;
@@ -570,6 +586,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_pool_big(PoolArgs a)
 
 __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
 {
+    pdl_enter();
     extern __shared__ int smem[];
     __shared__ TestSpec spec;
     __shared__ GroupState S;
@@ -600,6 +617,7 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
                         const long long* __restrict__ binom, int32_t* __restrict__ sep_pool, long long sep_cap,
                         DepthCounters* ctr)
 {
+    pdl_enter();
     if (!ctr->active) return;
     const int d = ctr->d;
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
@@ -655,6 +673,7 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
 __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
                             unsigned long long* cursor)
 {
+    pdl_enter();
     if (!ctr->active) return;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -745,12 +764,30 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
 
 // --------------------------------------------------------------------------
 // host launchers
+
+// Launch with programmatic stream serialisation (see pdl_enter).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
                      int total_vertices, DepthCounters* ctr, cudaStream_t st)
 {
     const int warps = 8;
-    k_snapshot<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(probs, vtx_prob, vtx_first,
-                                                                           total_vertices, ctr);
+    launch_pdl(k_snapshot, dim3((total_vertices + warps - 1) / warps), dim3(warps * 32), 0, st, probs, vtx_prob,
+               vtx_first, total_vertices, ctr);
 }
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
@@ -760,9 +797,9 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
                   unsigned long long* hist, cudaStream_t st)
 {
     const int warps = 8;
-    k_edges<<<(total_vertices + warps - 1) / warps, warps * 32, 0, st>>>(
-        probs, vtx_prob, vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, edges,
-        min_accept, edge_cap, ctr, hist);
+    launch_pdl(k_edges, dim3((total_vertices + warps - 1) / warps), dim3(warps * 32), 0, st, probs, vtx_prob,
+               vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, edges, min_accept,
+               edge_cap, ctr, hist);
 }
 
 void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
@@ -771,33 +808,34 @@ void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCount
                   int forced_group, long long smem_ints, long long split_stride, int allow_split, int grid,
                   cudaStream_t st)
 {
-    k_scan<<<1, 1024, 0, st>>>(hist, cls, ctr, alive, base, groups[0], groups[1], groups[2], groups[3], mean_n,
-                               forced_group, smem_ints, split_stride, allow_split);
-    k_place<<<grid, 256, 0, st>>>(edges, edge_cap, cls, ctr, alive, cursor, sorted);
+    launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, hist, cls, ctr, alive, base, groups[0], groups[1], groups[2],
+               groups[3], mean_n, forced_group, smem_ints, split_stride, allow_split);
+    launch_pdl(k_place, dim3(grid), dim3(256), 0, st, edges, edge_cap, cls, ctr, alive, cursor, sorted);
 }
 
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st)
 {
-    if (cls == kClassWarp) k_pool_small<<<grid, kTestThreads, smem_bytes, st>>>(a);
-    else k_pool_big<<<grid, kTestThreads, smem_bytes, st>>>(a);
+    if (cls == kClassWarp) launch_pdl(k_pool_small, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
+    else launch_pdl(k_pool_big, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
 }
 
 void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st)
 {
-    k_plain<<<grid, kTestThreads, smem_bytes, st>>>(a);
+    launch_pdl(k_plain, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
 }
 
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
                   long long edge_cap, const long long* binom, int32_t* sep_pool, long long sep_cap,
                   DepthCounters* ctr, int grid, cudaStream_t st)
 {
-    k_apply<<<grid, 256, 0, st>>>(probs, edges, min_accept, edge_cap, binom, sep_pool, sep_cap, ctr);
+    launch_pdl(k_apply, dim3(grid), dim3(256), 0, st, probs, edges, min_accept, edge_cap, binom, sep_pool, sep_cap,
+               ctr);
 }
 
 void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
                       unsigned long long* cursor, cudaStream_t st)
 {
-    k_depth_end<<<1, 256, 0, st>>>(ctr, rec, max_depth, hist, cursor);
+    launch_pdl(k_depth_end, dim3(1), dim3(256), 0, st, ctr, rec, max_depth, hist, cursor);
 }
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
