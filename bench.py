@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
     ap.add_argument("--depth1", choices=["auto", "pool", "tensor"], default="auto",
                     help="depth-1 counting: tensor-core neighbourhood product or work pool")
+    ap.add_argument("--ablation", action="store_true",
+                    help="instead of the bench line: the group-size, granularity, sample-size and network-size "
+                         "studies, one JSON line per configuration")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -250,8 +253,74 @@ def run_reference(args, w, name, rank, world):
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_ablation(args):
+    """The studies of the paper's Section V on synthetic networks: group size gs
+    (tests executed vs time), granularity (CI-level pool, edge-level plain form,
+    threads per test), sample size and network size.  Each configuration: 2
+    untimed skeletons, then the median of 5 timed ones (CUDA events, L2 flushed
+    before each); the oracle's sequential rate is sampled for the sample-size
+    study."""
+    import bnsynth
+    import torch
+    import paper_2212_04259_gb300 as F
+    from paper_2212_04259_gb300 import build
+    build.build()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")
+
+    def measure(data, ar, alpha, md, **opt):
+        h = F.fbn_create(torch.from_numpy(data).cuda(), ar, **opt)
+        F.fbn_set_stream(h, stream)
+        for _ in range(2):
+            F.fbn_learn_skeleton(h, alpha, md)
+        ms = []
+        for _ in range(5):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            F.fbn_learn_skeleton(h, alpha, md)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = F.fbn_get_stats(h)
+        F.fbn_destroy(h)
+        med = statistics.median(ms)
+        return {"ms": med, "tests_executed": sum(st["tests"]), "tests_oracle": sum(st["tests_oracle"]),
+                "tests_per_s": sum(st["tests_oracle"]) / (med / 1e3), "depths": st["depths"]}
+
+    def emit(kind, config, res):
+        print(json.dumps({"ablation": kind, "config": config, **res}), flush=True)
+
+    data, ar, alpha, md, _ = bnsynth.workload("mid")
+    for gs in (1, 2, 4, 8, 16, 0):
+        emit("group_size", {"workload": "mid", "gs": gs or "per depth (1 or 4)"},
+             measure(data, ar, alpha, md, group_size=gs))
+    for label, opt in (("CI-level work pool", {}), ("edge-level plain form", {"form": "plain"}),
+                       ("CI-level, 32 threads per test", {"group_threads": 32}),
+                       ("CI-level, 256 threads per test", {"group_threads": 256})):
+        for wl in ("mid", "large"):
+            d2, a2, al2, md2, _ = bnsynth.workload(wl)
+            emit("granularity", {"workload": wl, "scheme": label}, measure(d2, a2, al2, md2, **opt))
+    import oracle
+    for N in (5000, 10000, 15000, 50000):
+        d2, a2, al2, md2, _ = bnsynth.workload("mid", n_samples=N)
+        res = measure(d2, a2, al2, md2)
+        t0 = time.perf_counter()
+        ref = oracle.pc_stable(d2, a2, al2, md2)
+        cpu_s = time.perf_counter() - t0
+        res.update(oracle_tests_per_s=ref.n_tests / cpu_s, oracle_cores=1,
+                   speedup_vs_oracle=(ref.n_tests / cpu_s and res["tests_per_s"] / (ref.n_tests / cpu_s)))
+        emit("sample_size", {"workload": "mid network", "n_samples": N}, res)
+    for wl in ("small", "mid", "large"):
+        d2, a2, al2, md2, _ = bnsynth.workload(wl)
+        emit("network_size", {"workload": wl, "n_vars": int(d2.shape[0]), "n_samples": int(d2.shape[1])},
+             measure(d2, a2, al2, md2))
+
+
 def main():
     args = parse()
+    if args.ablation:
+        return run_ablation(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
