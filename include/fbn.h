@@ -174,6 +174,22 @@ int32_t fbn_get_sepset(const fbn_handle* h, int32_t i, int32_t j, int32_t* buf, 
 int fbn_export_sepsets(const fbn_handle* h, int64_t* n_removed, int64_t* n_members,
                        int32_t* pairs, int64_t* offsets, int32_t* members);
 
+/* fbn_orient_cpdag -- steps 2 and 3 of PC-stable (Section II-C) on the last
+ * skeleton: v-structures from the separating sets, then Meek's orientation
+ * rules, giving the completed partially directed graph (host code; the
+ * skeleton is the hot path).
+ *   cpdag_out : uint8 [n][n], host, caller-owned.  cpdag_out[a][b] = 1 and
+ *               cpdag_out[b][a] = 0 for a directed edge a -> b; both 1 for an
+ *               undirected edge; both 0 for no edge.
+ * v-structures: every unshielded triple a - k - b (a, b not adjacent) with k
+ * outside SepSet(a, b) marks a -> k and b -> k, all triples judged on the
+ * skeleton alone; an edge marked both ways stays undirected.  Meek rules
+ * R1-R3 then run in rounds, each round applying at once every orientation a
+ * rule implies on the current graph except those implied both ways, until a
+ * round changes nothing.  The result does not depend on variable order.
+ * Errors: FBN_EINVAL (NULL, or no skeleton learnt yet). */
+int fbn_orient_cpdag(const fbn_handle* h, uint8_t* cpdag_out);
+
 /* fbn_get_stats -- per-depth counters of the last skeleton call. */
 int fbn_get_stats(const fbn_handle* h, fbn_stats* out);
 

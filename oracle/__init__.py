@@ -15,10 +15,12 @@ passage of the Fast-BNS paper it follows:
 * ``chisq_sf``   -- chi-square survival function, exact finite sums for integer df;
 * ``ci_test``    -- one CI test and its decision rule, Section III-B;
 * ``subsets``    -- conditioning sets in lexicographic order, Section IV-C;
-* ``pc_stable``  -- Algorithm 1 with endpoint grouping (Section IV-C).
+* ``pc_stable``  -- Algorithm 1 with endpoint grouping (Section IV-C);
+* ``orient_cpdag`` -- steps 2-3 of PC-stable (Section II-C): v-structures and
+  Meek's rules, in ``cpdag.py`` (plain Python).
 
 Parity is pinned for every function above by the CPU tests in
-``tests/test_oracle_pins.py``.
+``tests/test_oracle_pins.py`` and ``tests/test_oracle_cpdag.py``.
 """
 from __future__ import annotations
 
@@ -198,3 +200,6 @@ def pc_stable(data, arities, alpha: float, max_depth: int = -1, near_tol: float 
     finally:
         lib.oracle_result_free(h)
     return PCResult(adj, sepsets, tests, removed, near)
+
+
+from .cpdag import orient_cpdag  # noqa: E402

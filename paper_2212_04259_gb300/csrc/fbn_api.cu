@@ -1330,6 +1330,98 @@ int fbn_export_sepsets(const fbn_handle* hc, int64_t* n_removed, int64_t* n_memb
     return FBN_OK;
 }
 
+int fbn_orient_cpdag(const fbn_handle* hc, uint8_t* cpdag_out)
+{
+    if (!hc || !hc->learnt || !cpdag_out) return FBN_EINVAL;
+    fbn_handle* h = const_cast<fbn_handle*>(hc);   // the host copy is a cache of device results
+    if (h->sep_pending) {
+        const int rc = materialize_sepsets(h, h->ws);
+        if (rc) return rc;
+    }
+    const int n = h->n;
+    const size_t nn = (size_t)n * n;
+    std::vector<uint8_t> A(nn);
+    CK(cudaSetDevice(h->device));
+    CK(cudaMemcpyAsync(A.data(), h->d_adj, nn, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<std::vector<int>> nb(n);
+    for (int u = 0; u < n; ++u)
+        for (int v = 0; v < n; ++v)
+            if (A[(size_t)u * n + v]) nb[u].push_back(v);
+    auto adj = [&](int u, int v) { return A[(size_t)u * n + v] != 0; };
+    auto in_sepset = [&](int a, int b, int k) {   // a < b, not adjacent
+        const size_t ab = (size_t)a * n + b;
+        const int32_t L = h->sep_len[ab];
+        for (int t = 0; t < L; ++t)
+            if (h->sep_members[(size_t)h->sep_off[ab] + t] == k) return true;
+        return false;
+    };
+    // step 2: arrowheads of the unshielded colliders
+    std::vector<uint8_t> head(nn, 0);   // head[a*n+k]: a -> k marked
+    for (int k = 0; k < n; ++k) {
+        const std::vector<int>& N = nb[k];
+        for (size_t x = 0; x < N.size(); ++x)
+            for (size_t y = x + 1; y < N.size(); ++y) {
+                const int a = N[x], b = N[y];
+                if (adj(a, b) || in_sepset(a, b, k)) continue;
+                head[(size_t)a * n + k] = 1;
+                head[(size_t)b * n + k] = 1;
+            }
+    }
+    std::vector<uint8_t> arc(nn, 0);    // arc[a*n+b]: a -> b oriented
+    for (size_t e = 0; e < nn; ++e) {
+        const size_t a = e / n, b = e % n;
+        if (head[e] && !head[b * n + a]) arc[e] = 1;
+    }
+    auto open = [&](int u, int v) { return adj(u, v) && !arc[(size_t)u * n + v] && !arc[(size_t)v * n + u]; };
+    // step 3: Meek rules in rounds
+    std::vector<std::pair<int, int>> found;
+    std::vector<uint8_t> want(nn, 0);
+    for (;;) {
+        found.clear();
+        for (int b = 0; b < n; ++b)
+            for (int c : nb[b]) {
+                if (!open(b, c)) continue;
+                bool orient = false;
+                for (int a : nb[b]) {
+                    if (a != c && arc[(size_t)a * n + b] && !adj(a, c)) orient = true;      // R1
+                    if (arc[(size_t)b * n + a] && arc[(size_t)a * n + c]) orient = true;  // R2
+                    if (orient) break;
+                }
+                if (!orient) {   // R3: two non-adjacent m1, m2 with b - m -> c
+                    std::vector<int> mids;
+                    for (int m : nb[b])
+                        if (open(b, m) && arc[(size_t)m * n + c]) mids.push_back(m);
+                    for (size_t x = 0; x < mids.size() && !orient; ++x)
+                        for (size_t y = x + 1; y < mids.size(); ++y)
+                            if (!adj(mids[x], mids[y])) {
+                                orient = true;
+                                break;
+                            }
+                }
+                if (orient) {
+                    found.emplace_back(b, c);
+                    want[(size_t)b * n + c] = 1;
+                }
+            }
+        bool changed = false;
+        for (const auto& bc : found) {
+            const size_t fw = (size_t)bc.first * n + bc.second, bw = (size_t)bc.second * n + bc.first;
+            if (!want[bw]) {
+                arc[fw] = 1;
+                changed = true;
+            }
+        }
+        for (const auto& bc : found) want[(size_t)bc.first * n + bc.second] = 0;
+        if (!changed) break;
+    }
+    for (size_t e = 0; e < nn; ++e) {
+        const size_t a = e / n, b = e % n;
+        cpdag_out[e] = (A[e] && !arc[b * n + a]) ? 1 : 0;
+    }
+    return FBN_OK;
+}
+
 int fbn_get_stats(const fbn_handle* h, fbn_stats* out)
 {
     if (!h || !out) return FBN_EINVAL;

@@ -25,7 +25,7 @@ MAX_DEPTHS = 64
 
 # Every symbol include/fbn.h declares.
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
-           "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_get_stats",
+           "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_orient_cpdag", "fbn_get_stats",
            "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
            "fbn_update_data")
 
@@ -83,6 +83,8 @@ def lib():
         L.fbn_export_sepsets.argtypes = [p, p, p, p, p, p]
         L.fbn_get_stats.restype = C.c_int
         L.fbn_get_stats.argtypes = [p, p]
+        L.fbn_orient_cpdag.restype = C.c_int
+        L.fbn_orient_cpdag.argtypes = [p, p]
         L.fbn_last_error.restype = C.c_char_p
         L.fbn_last_error.argtypes = [p]
         L.fbn_destroy.restype = None
@@ -256,6 +258,14 @@ def fbn_export_sepsets(h: Handle, as_dict: bool = True):
         return pairs[: nr.value], offs, mem[: nm.value]
     return {(int(pairs[k, 0]), int(pairs[k, 1])): tuple(int(v) for v in mem[offs[k]:offs[k + 1]])
             for k in range(nr.value)}
+
+
+def fbn_orient_cpdag(h: Handle) -> np.ndarray:
+    """CPDAG of the last skeleton (v-structures + Meek rules): uint8 [n][n],
+    M[a][b] = 1, M[b][a] = 0 for a -> b; both 1 for an undirected edge."""
+    out = np.zeros((h.n, h.n), dtype=np.uint8)
+    _check(lib().fbn_orient_cpdag(h.ptr, _ptr(out)), h)
+    return out
 
 
 def fbn_get_stats(h: Handle) -> dict:
