@@ -11,6 +11,8 @@ passage of the Fast-BNS paper it follows:
 
 * ``ci_table``   -- contingency table, Section III-B / Section IV-A step (i);
 * ``g2``         -- G^2 statistic and expected counts, Section III-B;
+* ``x2``         -- Pearson's X^2 of the same table, Section III-B;
+* ``df_adjusted``-- degrees of freedom of the observed table (skeleton variant);
 * ``df``         -- degrees of freedom, Section III-B (conditional form);
 * ``chisq_sf``   -- chi-square survival function, exact finite sums for integer df;
 * ``ci_test``    -- one CI test and its decision rule, Section III-B;
@@ -67,12 +69,20 @@ def _load():
         lib.oracle_chisq_sf.argtypes = [i64, f64]
         lib.oracle_ci_test.restype = C.c_int
         lib.oracle_ci_test.argtypes = [p, i64, i64, p, i32, i32, p, i32, p, p, p]
+        lib.oracle_ci_test_ex.restype = C.c_int
+        lib.oracle_ci_test_ex.argtypes = [p, i64, i64, p, i32, i32, p, i32, i32, i32, p, p, p]
+        lib.oracle_x2.restype = f64
+        lib.oracle_x2.argtypes = [p, i32, i32, i64]
+        lib.oracle_df_adjusted.restype = f64
+        lib.oracle_df_adjusted.argtypes = [p, i32, i32, i64]
         lib.oracle_first_subset.restype = C.c_int
         lib.oracle_first_subset.argtypes = [i32, i32, p]
         lib.oracle_next_subset.restype = C.c_int
         lib.oracle_next_subset.argtypes = [i32, i32, p]
         lib.oracle_pc_stable.restype = p
         lib.oracle_pc_stable.argtypes = [p, i64, i32, i64, p, f64, i32, f64]
+        lib.oracle_pc_stable_ex.restype = p
+        lib.oracle_pc_stable_ex.argtypes = [p, i64, i32, i64, p, f64, i32, f64, i32, i32]
         lib.oracle_result_free.argtypes = [p]
         lib.oracle_result_adjacency.argtypes = [p, p]
         lib.oracle_result_sepset.restype = i32
@@ -121,6 +131,25 @@ def g2(counts, rx: int, ry: int) -> float:
     return _load().oracle_g2(_ptr(counts), rx, ry, counts.size // (rx * ry))
 
 
+def x2(counts, rx: int, ry: int) -> float:
+    """Pearson's X^2 of a flat table, layout as g2 (Section III-B names it next to G^2)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64).ravel()
+    assert counts.size % (rx * ry) == 0
+    return _load().oracle_x2(_ptr(counts), rx, ry, counts.size // (rx * ry))
+
+
+def df_adjusted(counts, rx: int, ry: int) -> float:
+    """Degrees of freedom of the observed table: sum over non-empty strata of
+    (values of X seen - 1)(values of Y seen - 1)."""
+    counts = np.ascontiguousarray(counts, dtype=np.int64).ravel()
+    assert counts.size % (rx * ry) == 0
+    return _load().oracle_df_adjusted(_ptr(counts), rx, ry, counts.size // (rx * ry))
+
+
+STATS = {"g2": 0, "x2": 1}
+DF_MODES = {"fixed": 0, "adjusted": 1}
+
+
 def df(arities, x: int, y: int, S=()) -> float:
     arities = np.ascontiguousarray(arities, dtype=np.uint8)
     S = np.ascontiguousarray(S, dtype=np.int32)
@@ -132,13 +161,16 @@ def chisq_sf(k: int, x: float) -> float:
     return _load().oracle_chisq_sf(int(k), float(x))
 
 
-def ci_test(data, arities, x: int, y: int, S=()):
-    """(G^2, df, p) of I(X, Y | S) (Section III-B)."""
+def ci_test(data, arities, x: int, y: int, S=(), stat: str = "g2", df_mode: str = "fixed"):
+    """(statistic, df, p) of I(X, Y | S) (Section III-B): G^2 or Pearson X^2,
+    df from the declared arities or adjusted to the observed table (p = 1
+    when no degree of freedom is left)."""
     data, arities = _prep(data, arities)
     S = np.ascontiguousarray(S, dtype=np.int32)
     out = np.zeros(3, dtype=np.float64)
-    rc = _load().oracle_ci_test(_ptr(data), data.shape[1], data.shape[1], _ptr(arities), x, y,
-                                _ptr(S), len(S), _ptr(out[0:]), _ptr(out[1:]), _ptr(out[2:]))
+    rc = _load().oracle_ci_test_ex(_ptr(data), data.shape[1], data.shape[1], _ptr(arities), x, y,
+                                   _ptr(S), len(S), STATS[stat], DF_MODES[df_mode],
+                                   _ptr(out[0:]), _ptr(out[1:]), _ptr(out[2:]))
     assert rc == 0
     return float(out[0]), float(out[1]), float(out[2])
 
@@ -169,13 +201,15 @@ class PCResult:
         return int(sum(self.tests))
 
 
-def pc_stable(data, arities, alpha: float, max_depth: int = -1, near_tol: float = 1e-6) -> PCResult:
-    """PC-stable skeleton (Algorithm 1) with the grouping of Section IV-C."""
+def pc_stable(data, arities, alpha: float, max_depth: int = -1, near_tol: float = 1e-6, stat: str = "g2",
+              df_mode: str = "fixed") -> PCResult:
+    """PC-stable skeleton (Algorithm 1) with the grouping of Section IV-C;
+    the CI test as in ci_test."""
     data, arities = _prep(data, arities)
     lib = _load()
     n, N = data.shape
-    h = lib.oracle_pc_stable(_ptr(data), N, n, N, _ptr(arities), float(alpha), int(max_depth),
-                             float(near_tol))
+    h = lib.oracle_pc_stable_ex(_ptr(data), N, n, N, _ptr(arities), float(alpha), int(max_depth),
+                                float(near_tol), STATS[stat], DF_MODES[df_mode])
     if not h:
         raise MemoryError("oracle_pc_stable failed")
     try:

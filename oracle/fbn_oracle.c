@@ -86,6 +86,60 @@ double oracle_g2(const int64_t* counts, int32_t rx, int32_t ry, int64_t nz)
     return 2.0 * g2;
 }
 
+/* Pearson's X^2 of the same table (the chi-square statistic the paper names
+ * next to G^2, Section III-B): sum over cells with E_xyz > 0 of
+ * (N_xyz - E_xyz)^2 / E_xyz.  With E = N_x+z N_+yz / N_++z each term is
+ * (N_xyz N_++z - N_x+z N_+yz)^2 / (N_++z N_x+z N_+yz): the numerator's
+ * difference is an exact 64-bit integer.  Empty cells with E > 0 count. */
+double oracle_x2(const int64_t* counts, int32_t rx, int32_t ry, int64_t nz)
+{
+    double x2 = 0.0;
+    for (int64_t z = 0; z < nz; z++) {
+        const int64_t* t = counts + z * rx * ry;
+        int64_t nzz = 0;
+        for (int32_t i = 0; i < rx * ry; i++) nzz += t[i];
+        if (nzz == 0) continue;
+        for (int32_t x = 0; x < rx; x++) {
+            int64_t nxz = 0;
+            for (int32_t y = 0; y < ry; y++) nxz += t[x * ry + y];
+            if (nxz == 0) continue;
+            for (int32_t y = 0; y < ry; y++) {
+                int64_t nyz = 0;
+                for (int32_t xx = 0; xx < rx; xx++) nyz += t[xx * ry + y];
+                if (nyz == 0) continue;
+                double diff = (double)(t[x * ry + y] * nzz - nxz * nyz);
+                x2 += diff * diff / ((double)nzz * (double)nxz * (double)nyz);
+            }
+        }
+    }
+    return x2;
+}
+
+/* Degrees of freedom adjusted to the observed table: the sum over strata with
+ * N_++z > 0 of (r'_x - 1)(r'_y - 1), r'_x counting the values of X with
+ * N_x+z > 0 in the stratum and r'_y those of Y with N_+yz > 0 (the variant of
+ * df that drops structurally empty rows, columns and strata). */
+double oracle_df_adjusted(const int64_t* counts, int32_t rx, int32_t ry, int64_t nz)
+{
+    double df = 0.0;
+    for (int64_t z = 0; z < nz; z++) {
+        const int64_t* t = counts + z * rx * ry;
+        int32_t ax = 0, ay = 0;
+        for (int32_t x = 0; x < rx; x++) {
+            int64_t s = 0;
+            for (int32_t y = 0; y < ry; y++) s += t[x * ry + y];
+            ax += s > 0;
+        }
+        for (int32_t y = 0; y < ry; y++) {
+            int64_t s = 0;
+            for (int32_t x = 0; x < rx; x++) s += t[x * ry + y];
+            ay += s > 0;
+        }
+        if (ax > 0 && ay > 0) df += (double)(ax - 1) * (double)(ay - 1);
+    }
+    return df;
+}
+
 /* Degrees of freedom (Section III-B, read as the conditional form; see header). */
 double oracle_df(const uint8_t* arities, int32_t x, int32_t y, const int32_t* S, int32_t d)
 {
@@ -125,23 +179,34 @@ double oracle_chisq_sf(int64_t k, double x)
     return q > 1.0 ? 1.0 : q;
 }
 
-/* One CI test I(X, Y | S): table, G^2, df and p (Section III-B). */
-int oracle_ci_test(const uint8_t* data, int64_t ld, int64_t n_samples, const uint8_t* arities,
-                   int32_t x, int32_t y, const int32_t* S, int32_t d,
-                   double* g2_out, double* df_out, double* p_out)
+/* One CI test I(X, Y | S): table, statistic, df and p (Section III-B).
+ * stat: 0 = G^2, 1 = Pearson X^2; df_mode: 0 = declared arities, 1 = adjusted
+ * to the observed table.  With no degrees of freedom left the test cannot
+ * reject: p = 1. */
+int oracle_ci_test_ex(const uint8_t* data, int64_t ld, int64_t n_samples, const uint8_t* arities,
+                      int32_t x, int32_t y, const int32_t* S, int32_t d, int32_t stat, int32_t df_mode,
+                      double* stat_out, double* df_out, double* p_out)
 {
     int64_t cells = (int64_t)arities[x] * arities[y];
     for (int32_t k = 0; k < d; k++) cells *= arities[S[k]];
     int64_t* counts = (int64_t*)malloc((size_t)cells * sizeof(int64_t));
     if (!counts) return ORACLE_ENOMEM;
     oracle_ci_table(data, ld, n_samples, arities, x, y, S, d, counts, cells);
-    double g2 = oracle_g2(counts, arities[x], arities[y], cells / ((int64_t)arities[x] * arities[y]));
-    double df = oracle_df(arities, x, y, S, d);
+    const int64_t nz = cells / ((int64_t)arities[x] * arities[y]);
+    double st = stat == 1 ? oracle_x2(counts, arities[x], arities[y], nz) : oracle_g2(counts, arities[x], arities[y], nz);
+    double df = df_mode == 1 ? oracle_df_adjusted(counts, arities[x], arities[y], nz) : oracle_df(arities, x, y, S, d);
     free(counts);
-    *g2_out = g2;
+    *stat_out = st;
     *df_out = df;
-    *p_out = oracle_chisq_sf((int64_t)df, g2);
+    *p_out = df > 0.0 ? oracle_chisq_sf((int64_t)df, st) : 1.0;
     return ORACLE_OK;
+}
+
+int oracle_ci_test(const uint8_t* data, int64_t ld, int64_t n_samples, const uint8_t* arities,
+                   int32_t x, int32_t y, const int32_t* S, int32_t d,
+                   double* g2_out, double* df_out, double* p_out)
+{
+    return oracle_ci_test_ex(data, ld, n_samples, arities, x, y, S, d, 0, 0, g2_out, df_out, p_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -214,9 +279,9 @@ void oracle_result_free(oracle_result* r)
     free(r);
 }
 
-oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int64_t n_samples,
-                                const uint8_t* arities, double alpha, int32_t max_depth,
-                                double near_tol)
+oracle_result* oracle_pc_stable_ex(const uint8_t* data, int64_t ld, int32_t n, int64_t n_samples,
+                                   const uint8_t* arities, double alpha, int32_t max_depth, double near_tol,
+                                   int32_t stat, int32_t df_mode)
 {
     oracle_result* r = (oracle_result*)calloc(1, sizeof(oracle_result));
     if (!r) return NULL;
@@ -280,7 +345,8 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
                     do {
                         for (int32_t k = 0; k < d; k++) S[k] = cand[c[k]];
                         double g2, df, pv;
-                        if (oracle_ci_test(data, ld, n_samples, arities, i, j, S, d, &g2, &df, &pv)) {
+                        if (oracle_ci_test_ex(data, ld, n_samples, arities, i, j, S, d, stat, df_mode, &g2, &df,
+                                              &pv)) {
                             free(nbr); free(deg); free(cand); free(c); free(S); free(remove);
                             oracle_result_free(r);
                             return NULL;
@@ -311,6 +377,12 @@ oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int6
     }
     free(nbr); free(deg); free(cand); free(c); free(S); free(remove);
     return r;
+}
+
+oracle_result* oracle_pc_stable(const uint8_t* data, int64_t ld, int32_t n, int64_t n_samples,
+                                const uint8_t* arities, double alpha, int32_t max_depth, double near_tol)
+{
+    return oracle_pc_stable_ex(data, ld, n, n_samples, arities, alpha, max_depth, near_tol, 0, 0);
 }
 
 void oracle_result_adjacency(const oracle_result* r, uint8_t* out)
