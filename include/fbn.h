@@ -46,6 +46,13 @@ extern "C" {
 #define FBN_DEPTH1_POOL   1  /* depth 1 through the work pool */
 #define FBN_DEPTH1_TENSOR 2  /* depth 1 through the tcgen05 neighbourhood product (arities <= 8, else FBN_EINVAL) */
 
+#define FBN_STAT_G2 0      /* G^2 = 2 sum N ln(N / E) (Section III-B) */
+#define FBN_STAT_X2 1      /* Pearson's X^2 = sum (N - E)^2 / E over cells with E > 0, same table and df */
+
+#define FBN_DF_FIXED    0  /* df = (r_x - 1)(r_y - 1) prod r_z from the declared arities */
+#define FBN_DF_ADJUSTED 1  /* df = sum over strata with N_++z > 0 of (values of X seen - 1)(values of Y seen - 1);
+                              a test with df = 0 cannot reject (p = 1) */
+
 typedef struct fbn_options {
     int32_t form;        /* FBN_FORM_POOL (default) or FBN_FORM_PLAIN */
     int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default (1) */
@@ -57,7 +64,9 @@ typedef struct fbn_options {
                             tensor-core pipeline) */
     int32_t depth1;      /* FBN_DEPTH1_*: how depth 1 counts its tables (pool form only); every test of a
                             vertex's neighbourhood at once on the tensor cores, or the work pool */
-    int32_t reserved[9]; /* must be zero */
+    int32_t statistic;   /* FBN_STAT_G2 (default) or FBN_STAT_X2: the statistic of every CI test */
+    int32_t df_mode;     /* FBN_DF_FIXED (default) or FBN_DF_ADJUSTED: degrees of freedom of every CI test */
+    int32_t reserved[7]; /* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */

@@ -416,6 +416,7 @@ bool use_nbr1(fbn_handle* const* hs, int k)
 {
     const fbn_handle* h = hs[0];
     if (h->opt.form == FBN_FORM_PLAIN || h->opt.depth1 != FBN_DEPTH1_TENSOR) return false;
+    if (h->opt.statistic != FBN_STAT_G2 || h->opt.df_mode != FBN_DF_FIXED) return false;
     for (int p = 0; p < k; ++p)
         if (hs[p]->max_arity > nbr1_max_arity()) return false;
     return true;
@@ -704,6 +705,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     base.binom_rows = ws.brows;
     base.crit = ct;
     base.alpha = alpha;
+    base.stat = h->opt.statistic;
+    base.df_mode = h->opt.df_mode;
     base.split_tab = ws.split_tab;
     base.split_ticket = ws.split_ticket;
     base.split_stride = kSplitStride;
@@ -780,6 +783,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         put(ptrs, sizeof ptrs);
         const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
                                   grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain, max_ar,
+                                  h->opt.statistic, h->opt.df_mode,
                                   groups[0], groups[1], groups[2], groups[3]};
         put(ints, sizeof ints);
         put(&mean_n, sizeof mean_n);
@@ -822,7 +826,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             rc = run_gram(h, ws, k, total_vtx, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS],
                           ws.kev[2 * FBN_MAX_DEPTHS + 1]);
             if (rc) return rc;
-            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr, grid_aux, st));
+            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr,
+                                   h->opt.statistic, h->opt.df_mode, grid_aux, st));
             CK(cudaEventRecord(ws.gkev[par][1], st));
             rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
             if (rc) return rc;
@@ -992,7 +997,8 @@ int run_ci(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, lo
     CK(cudaMemcpyAsync(h->d_ci, h->h_ci, sizeof(CiTestDesc), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     launch_ci_tests(h->d_prob, h->d_ci, 1, h->d_ci_out, want_table ? h->d_table : nullptr,
-                    gints ? h->d_gscratch : nullptr, gints, h->d_status, kSmemBytes, st);
+                    gints ? h->d_gscratch : nullptr, gints, h->d_status, kSmemBytes, h->opt.statistic, h->opt.df_mode,
+                    st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_ci_out, h->d_ci_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -1041,7 +1047,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 9; ++k)
+        for (int k = 0; k < 7; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
         if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
         if (o.group_threads != 0 && o.group_threads != 32 && o.group_threads != 64 && o.group_threads != 128 &&
@@ -1051,6 +1057,12 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         if (o.group_size < 0) return fail(nullptr, FBN_EINVAL, "bad group_size %d", o.group_size);
         if (o.depth0 < FBN_DEPTH0_AUTO || o.depth0 > FBN_DEPTH0_GRAM) return fail(nullptr, FBN_EINVAL, "bad depth0 %d", o.depth0);
         if (o.depth1 < FBN_DEPTH1_AUTO || o.depth1 > FBN_DEPTH1_TENSOR) return fail(nullptr, FBN_EINVAL, "bad depth1 %d", o.depth1);
+        if (o.statistic != FBN_STAT_G2 && o.statistic != FBN_STAT_X2)
+            return fail(nullptr, FBN_EINVAL, "bad statistic %d", o.statistic);
+        if (o.df_mode != FBN_DF_FIXED && o.df_mode != FBN_DF_ADJUSTED)
+            return fail(nullptr, FBN_EINVAL, "bad df_mode %d", o.df_mode);
+        if (o.depth1 == FBN_DEPTH1_TENSOR && (o.statistic != FBN_STAT_G2 || o.df_mode != FBN_DF_FIXED))
+            return fail(nullptr, FBN_EINVAL, "depth1 tensor takes the G^2 statistic with fixed df only");
     }
     int max_ar = 0;
     for (int v = 0; v < n_vars; ++v) {

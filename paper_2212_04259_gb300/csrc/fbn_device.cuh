@@ -651,6 +651,55 @@ __device__ __forceinline__ double grp_g2_exact(const TestSpec& s, const int* T, 
     return 2.0 * grp_sum<G>(acc, red);
 }
 
+// CI-test statistics: G^2 (Section III-B) or Pearson's X^2 of the same table.
+constexpr int kStatG2 = 0;
+constexpr int kStatX2 = 1;
+
+// Exact Pearson X^2 = sum (N - E)^2 / E in FP64 over cells with E > 0 (empty
+// cells included), each term (N_xyz N_++z - N_x+z N_+yz)^2 / (N_++z N_x+z
+// N_+yz) with the difference an exact 64-bit integer.
+template <int G>
+__device__ __forceinline__ double grp_x2_exact(const TestSpec& s, const int* T, const int* M, double* red,
+                                               int32_t* table_out)
+{
+    const long long nz = s.cells / (s.rx * s.ry);
+    const int rxy = s.rx * s.ry;
+    const int* Nxz = M;
+    const int* Nyz = M + nz * s.rx;
+    const int* Nzz = Nyz + nz * s.ry;
+    double acc = 0.0;
+    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+        const int n = T[c];
+        if (table_out) table_out[c] = n;
+        const long long z = c / rxy;
+        const int rem = (int)(c - z * rxy);
+        const int x = rem / s.ry, y = rem - x * s.ry;
+        const long long nx = Nxz[z * s.rx + x], ny = Nyz[z * s.ry + y];
+        if (nx == 0 || ny == 0) continue;
+        const double dd = (double)((long long)n * Nzz[z] - nx * ny);
+        acc += dd * dd / ((double)Nzz[z] * (double)nx * (double)ny);
+    }
+    return grp_sum<G>(acc, red);
+}
+
+// Degrees of freedom of the observed table: sum over strata with N_++z > 0 of
+// (values of X with N_x+z > 0 - 1)(values of Y with N_+yz > 0 - 1).
+template <int G>
+__device__ __forceinline__ long long grp_df_adjusted(const TestSpec& s, const int* M, double* red)
+{
+    const long long nz = s.cells / (s.rx * s.ry);
+    const int* Nxz = M;
+    const int* Nyz = M + nz * s.rx;
+    double acc = 0.0;
+    for (long long z = Grp<G>::rank(); z < nz; z += G) {
+        int ax = 0, ay = 0;
+        for (int x = 0; x < s.rx; ++x) ax += Nxz[z * s.rx + x] > 0;
+        for (int y = 0; y < s.ry; ++y) ay += Nyz[z * s.ry + y] > 0;
+        if (ax > 0 && ay > 0) acc += (double)(ax - 1) * (double)(ay - 1);
+    }
+    return (long long)(grp_sum<G>(acc, red) + 0.5);
+}
+
 // Decision "p > alpha" as "G^2 < crit".  The terms are first evaluated with
 // FP32 logarithms -- each within 3.2e-7 of its own magnitude, CUDA's logf and
 // log1pf being within 1 ulp and the ratio formed from exact 64-bit integers --
@@ -659,9 +708,15 @@ __device__ __forceinline__ double grp_g2_exact(const TestSpec& s, const int* T, 
 // sum of magnitudes.  G^2 is thus within 2 (3.2e-7 + (ceil(C/G) + log2 G) 6e-8)
 // sum|term| of its exact value (doubled below for margin); only when crit lies
 // inside that band is G^2 recomputed exactly in FP64.
+//
+// X^2 (stat = kStatX2): each term D^2 / (N_++z N_x+z N_+yz) with D the exact
+// integer difference, formed in FP32 within 6e-7 of itself (three conversions,
+// a square, two products, a quotient); the terms are non-negative, so the
+// running sum of magnitudes is the sum itself, and the same summation bound
+// applies without the doubling of G^2.
 template <int G>
 __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, const int* M, double crit,
-                                           double* red)
+                                           double* red, int stat = kStatG2)
 {
     const long long nz = s.cells / (s.rx * s.ry);
     const int rxy = s.rx * s.ry;
@@ -669,20 +724,34 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
     const int* Nyz = M + nz * s.rx;
     const int* Nzz = Nyz + nz * s.ry;
     float acc = 0.0f, mag = 0.0f;
-    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
-        const int n = T[c];
-        if (n == 0) continue;
-        const long long z = c / rxy;
-        const int rem = (int)(c - z * rxy);
-        const int x = rem / s.ry, y = rem - x * s.ry;
-        const long long a = (long long)n * Nzz[z];
-        const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
-        const float fb = (float)b;
-        const float delta = (float)(a - b) / fb;
-        const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
-        const float t = (float)n * L;
-        acc += t;
-        mag += fabsf(t);
+    if (stat == kStatX2) {
+        for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+            const long long z = c / rxy;
+            const int rem = (int)(c - z * rxy);
+            const int x = rem / s.ry, y = rem - x * s.ry;
+            const int nx = Nxz[z * s.rx + x], ny = Nyz[z * s.ry + y];
+            if (nx == 0 || ny == 0) continue;
+            const float fd = (float)((long long)T[c] * Nzz[z] - (long long)nx * ny);
+            const float t = fd * fd / ((float)Nzz[z] * (float)nx * (float)ny);
+            acc += t;
+        }
+        mag = acc;
+    } else {
+        for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+            const int n = T[c];
+            if (n == 0) continue;
+            const long long z = c / rxy;
+            const int rem = (int)(c - z * rxy);
+            const int x = rem / s.ry, y = rem - x * s.ry;
+            const long long a = (long long)n * Nzz[z];
+            const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
+            const float fb = (float)b;
+            const float delta = (float)(a - b) / fb;
+            const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
+            const float t = (float)n * L;
+            acc += t;
+            mag += fabsf(t);
+        }
     }
     float2 v = make_float2(acc, mag);
 #pragma unroll
@@ -708,12 +777,14 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
     }
     const double per_thread = (double)((s.cells + G - 1) / G);
     const double levels = (G == 32 ? 5.0 : G == 64 ? 6.0 : G == 128 ? 7.0 : 8.0);
-    const double rel = 2.0 * (3.2e-7 + (per_thread + levels) * 6e-8);
-    const double g2 = 2.0 * (double)v.x;
-    const double err = 2.0 * rel * (double)v.y * 1.0001 + 1e-9;
-    if (g2 + err < crit) return true;
-    if (g2 - err >= crit) return false;
-    return grp_g2_exact<G>(s, T, M, red, nullptr) < crit;
+    const double term_rel = stat == kStatX2 ? 6e-7 : 3.2e-7;
+    const double rel = 2.0 * (term_rel + (per_thread + levels) * 6e-8);
+    const double scale = stat == kStatX2 ? 1.0 : 2.0;   // G^2 = 2 sum
+    const double st = scale * (double)v.x;
+    const double err = scale * rel * (double)v.y * 1.0001 + 1e-9;
+    if (st + err < crit) return true;
+    if (st - err >= crit) return false;
+    return (stat == kStatX2 ? grp_x2_exact<G>(s, T, M, red, nullptr) : grp_g2_exact<G>(s, T, M, red, nullptr)) < crit;
 }
 
 }  // namespace fbn

@@ -273,11 +273,12 @@ __global__ void k_onehot(const ProblemDev* __restrict__ probs, const int32_t* __
 
 // Decision of one depth-0 pair from its block of the Gram (row sums, column
 // sums and the total from the block itself).  R bounds the arities so that
-// the sums live in registers.
+// the sums live in registers.  stat: G^2 or Pearson X^2; df_mode: declared
+// arities or the observed table (no degree of freedom left: accept).
 template <int R>
 __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, int rx, int ry, long long e,
                                               unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                              double alpha, DepthCounters* ctr)
+                                              double alpha, DepthCounters* ctr, int stat, int df_mode)
 {
     int rs[R], cs[R];
     int tot = 0;
@@ -293,9 +294,22 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
                 cs[y] += nxy;
                 tot += nxy;
             }
-    // terms with FP32 logs summed in FP64 (each term within 3.2e-7 of its
-    // magnitude); exact FP64 only when crit lies inside the error band
-    const long long df = (long long)(rx - 1) * (ry - 1);
+    long long df = (long long)(rx - 1) * (ry - 1);
+    if (df_mode) {
+        int ax = 0, ay = 0;
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            ax += rs[q] > 0;
+            ay += cs[q] > 0;
+        }
+        df = ax > 0 && ay > 0 ? (long long)(ax - 1) * (ay - 1) : 0;
+    }
+    if (df <= 0) {   // p = 1 > alpha
+        min_accept[e] = 0;
+        return;
+    }
+    // terms in FP32 (G^2: within 3.2e-7 of their magnitude; X^2: within 6e-7)
+    // summed in FP64; exact FP64 only when crit lies inside the error band
     const double c = crit_get(crit, df, alpha, &ctr->status);
     double acc = 0.0, mag = 0.0;
 #pragma unroll
@@ -304,20 +318,29 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
         for (int y = 0; y < R; ++y) {
             if (x >= rx || y >= ry) continue;
             const int n = T[(long long)x * Mp + y];
-            if (n == 0) continue;
-            const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
-            const float fb = (float)b;
-            const float delta = (float)(a - b) / fb;
-            const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
-            acc += (double)((float)n * L);
-            mag += fabs((double)((float)n * L));
+            if (stat == kStatX2) {
+                if (rs[x] == 0 || cs[y] == 0) continue;
+                const float fd = (float)((long long)n * tot - (long long)rs[x] * cs[y]);
+                const float t = fd * fd / ((float)tot * (float)rs[x] * (float)cs[y]);
+                acc += (double)t;
+                mag += (double)t;
+            } else {
+                if (n == 0) continue;
+                const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
+                const float fb = (float)b;
+                const float delta = (float)(a - b) / fb;
+                const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
+                acc += (double)((float)n * L);
+                mag += fabs((double)((float)n * L));
+            }
         }
-    const double g2 = 2.0 * acc;
-    const double err = 2.0 * 2.0 * 3.2e-7 * mag * 1.0001 + 1e-9;
+    const double scale = stat == kStatX2 ? 1.0 : 2.0;
+    const double st = scale * acc;
+    const double err = scale * 2.0 * (stat == kStatX2 ? 6e-7 : 3.2e-7) * mag * 1.0001 + 1e-9;
     bool accept;
-    if (g2 + err < c) {
+    if (st + err < c) {
         accept = true;
-    } else if (g2 - err >= c) {
+    } else if (st - err >= c) {
         accept = false;
     } else {
         double ex = 0.0;
@@ -327,24 +350,49 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
             for (int y = 0; y < R; ++y) {
                 if (x >= rx || y >= ry) continue;
                 const int n = T[(long long)x * Mp + y];
-                if (n == 0) continue;
-                const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
-                ex += (double)n * log1p((double)(a - b) / (double)b);
+                if (stat == kStatX2) {
+                    if (rs[x] == 0 || cs[y] == 0) continue;
+                    const double dd = (double)((long long)n * tot - (long long)rs[x] * cs[y]);
+                    ex += dd * dd / ((double)tot * (double)rs[x] * (double)cs[y]);
+                } else {
+                    if (n == 0) continue;
+                    const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
+                    ex += (double)n * log1p((double)(a - b) / (double)b);
+                }
             }
-        accept = 2.0 * ex < c;
+        accept = scale * ex < c;
     }
     if (accept) min_accept[e] = 0;
 }
 
-// Arities above 8: the sums are recomputed from the block (no local arrays).
+// Arities above 8: the sums are recomputed from the block (no local arrays),
+// the statistic in FP64.
 __device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp, int rx, int ry, long long e,
                                                  unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                                 double alpha, DepthCounters* ctr)
+                                                 double alpha, DepthCounters* ctr, int stat, int df_mode)
 {
     long long tot = 0;
     for (int x = 0; x < rx; ++x)
         for (int y = 0; y < ry; ++y) tot += T[(long long)x * Mp + y];
-    const long long df = (long long)(rx - 1) * (ry - 1);
+    long long df = (long long)(rx - 1) * (ry - 1);
+    if (df_mode) {
+        int ax = 0, ay = 0;
+        for (int x = 0; x < rx; ++x) {
+            long long s = 0;
+            for (int y = 0; y < ry; ++y) s += T[(long long)x * Mp + y];
+            ax += s > 0;
+        }
+        for (int y = 0; y < ry; ++y) {
+            long long s = 0;
+            for (int x = 0; x < rx; ++x) s += T[(long long)x * Mp + y];
+            ay += s > 0;
+        }
+        df = ax > 0 && ay > 0 ? (long long)(ax - 1) * (ay - 1) : 0;
+    }
+    if (df <= 0) {
+        min_accept[e] = 0;
+        return;
+    }
     const double c = crit_get(crit, df, alpha, &ctr->status);
     double ex = 0.0;
     for (int x = 0; x < rx; ++x) {
@@ -352,42 +400,49 @@ __device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp,
         for (int y = 0; y < ry; ++y) rsx += T[(long long)x * Mp + y];
         for (int y = 0; y < ry; ++y) {
             const int n = T[(long long)x * Mp + y];
-            if (n == 0) continue;
             long long csy = 0;
             for (int xx = 0; xx < rx; ++xx) csy += T[(long long)xx * Mp + y];
-            const long long a = (long long)n * tot, b = rsx * csy;
-            ex += (double)n * log1p((double)(a - b) / (double)b);
+            if (stat == kStatX2) {
+                if (rsx == 0 || csy == 0) continue;
+                const double dd = (double)(n * tot - rsx * csy);
+                ex += dd * dd / ((double)tot * (double)rsx * (double)csy);
+            } else {
+                if (n == 0) continue;
+                const long long a = (long long)n * tot, b = rsx * csy;
+                ex += (double)n * log1p((double)(a - b) / (double)b);
+            }
         }
     }
-    if (2.0 * ex < c) min_accept[e] = 0;
+    if ((stat == kStatX2 ? 1.0 : 2.0) * ex < c) min_accept[e] = 0;
 }
 
 __device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, long long e,
                                             const ProblemDev* __restrict__ probs,
                                             unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                            double alpha, DepthCounters* ctr)
+                                            double alpha, DepthCounters* ctr, int stat, int df_mode)
 {
     const EdgeWork w = edges[e];
     const ProblemDev& P = probs[w.prob];
     const int rx = P.ar[w.i], ry = P.ar[w.j];
     const long long Mp = P.gram_ld;
     const int32_t* T = P.gram + (long long)P.off[w.i] * Mp + P.off[w.j];
-    if (rx <= 4 && ry <= 4) pair_decide_r<4>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
-    else if (rx <= 8 && ry <= 8) pair_decide_r<8>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
-    else pair_decide_wide(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr);
+    if (rx <= 4 && ry <= 4) pair_decide_r<4>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
+    else if (rx <= 8 && ry <= 8) pair_decide_r<8>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
+    else pair_decide_wide(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
 }
 
 // Depth-0 decisions from the Gram: one thread per edge (i<j) of both classes
 // of the edge list (class 0 at the front of the array, class 1 at the back).
 __global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long edge_cap,
                                const ProblemDev* __restrict__ probs, unsigned long long* __restrict__ min_accept,
-                               CritTableDev crit, double alpha, DepthCounters* ctr)
+                               CritTableDev crit, double alpha, DepthCounters* ctr, int stat, int df_mode)
 {
     if (!ctr->active) return;
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
          k += (long long)gridDim.x * blockDim.x)
-        pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, min_accept, crit, alpha, ctr);
+        pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, min_accept, crit, alpha, ctr, stat,
+                    df_mode);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctr->tests, (unsigned long long)(n0 + n1));   // one test per pair
 }
 // Zero the pad rows M..Mp of every problem's one-hot matrix (one CTA per
@@ -486,9 +541,9 @@ cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const 
 
 cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs,
                                 unsigned long long* min_accept, const CritTableDev& crit, double alpha,
-                                DepthCounters* ctr, int grid, cudaStream_t st)
+                                DepthCounters* ctr, int stat, int df_mode, int grid, cudaStream_t st)
 {
-    k_pairs_decide<<<grid, 256, 0, st>>>(edges, edge_cap, probs, min_accept, crit, alpha, ctr);
+    k_pairs_decide<<<grid, 256, 0, st>>>(edges, edge_cap, probs, min_accept, crit, alpha, ctr, stat, df_mode);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ cudaError_t launch_gram(const void* maps, const int4* units, int n_units, const 
                         unsigned* status, int wait_limit, cudaStream_t st);
 cudaError_t launch_pairs_decide(const EdgeWork* edges, long long edge_cap, const ProblemDev* probs,
                                 unsigned long long* min_accept, const CritTableDev& crit, double alpha,
-                                DepthCounters* ctr, int grid, cudaStream_t st);
+                                DepthCounters* ctr, int stat, int df_mode, int grid, cudaStream_t st);
 cudaError_t launch_symmetrize(int32_t* G, int Mp, int M, cudaStream_t st);
 
 }  // namespace fbn

@@ -149,6 +149,8 @@ struct PoolArgs {
     int* split_tab;                   // [kSplitItems][split_stride] zero global tables of split tests
     unsigned* split_ticket;           // [kSplitItems] parts finished per test, zero between uses
     long long split_stride;           // ints per split table
+    int32_t stat;                     // CI statistic: 0 = G^2, 1 = Pearson X^2
+    int32_t df_mode;                  // degrees of freedom: 0 = declared arities, 1 = observed table
 };
 
 }  // namespace fbn

@@ -381,6 +381,24 @@ __device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& 
     return true;
 }
 
+// The decision of a counted test from its table and marginals: df from the
+// declared arities or from the observed table (no degree of freedom left:
+// the test cannot reject), crit from the cache, then the bounded statistic.
+template <int G>
+__device__ __forceinline__ int decide_test(const PoolArgs& a, const TestSpec& spec, const int* T, const int* M,
+                                           GroupState& S, double* red, unsigned* status)
+{
+    const long long df = a.df_mode ? grp_df_adjusted<G>(spec, M, red)
+                                   : (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
+    if (Grp<G>::rank() == 0) {
+        S.crit = df > 0 ? crit_get(a.crit, df, a.alpha, status) : 0.0;
+        S.tests += 1;   // flushed to the depth counter when the group leaves the pool
+    }
+    Grp<G>::sync();
+    if (df <= 0) return 1;   // p = 1 > alpha
+    return grp_decide<G>(spec, T, M, S.crit, red, a.stat) ? 1 : 0;
+}
+
 // Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
 template <int G>
 __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w, long long rk,
@@ -399,13 +417,7 @@ __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemD
         return -1;
     }
     grp_marginals<G>(spec, T, M);
-    if (Grp<G>::rank() == 0) {
-        const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
-        S.crit = crit_get(a.crit, df, a.alpha, status);
-        S.tests += 1;   // flushed to the depth counter when the group leaves the pool
-    }
-    Grp<G>::sync();
-    return grp_decide<G>(spec, T, M, S.crit, red) ? 1 : 0;
+    return decide_test<G>(a, spec, T, M, S, red, status);
 }
 
 // One part of a split test: count samples [N p / S, N (p + 1) / S) (16-aligned
@@ -465,13 +477,7 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
     if (!S.go) return 0;
     int* M = Tl + C;
     grp_marginals<G>(spec, Tl, M);
-    if (r == 0) {
-        const long long df = (long long)(spec.rx - 1) * (spec.ry - 1) * (C / (spec.rx * spec.ry));
-        S.crit = crit_get(a.crit, df, a.alpha, status);
-        S.tests += 1;
-    }
-    Grp<G>::sync();
-    return grp_decide<G>(spec, Tl, M, S.crit, red) ? 1 : 0;
+    return decide_test<G>(a, spec, Tl, M, S, red, status);
 }
 
 // Shared state of a pool CTA, sized for the most groups per CTA (8 warps).
@@ -713,7 +719,7 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
                                                            const CiTestDesc* __restrict__ tests, int ntests,
                                                            double* __restrict__ out, int32_t* table_out,
                                                            int* gscratch, long long gscratch_ints,
-                                                           unsigned* status, int smem_ints)
+                                                           unsigned* status, int smem_ints, int stat, int df_mode)
 {
     extern __shared__ int smem[];
     __shared__ TestSpec spec;
@@ -753,12 +759,14 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
         return;
     }
     grp_marginals<kTestThreads>(spec, T, M);
-    const double g2 = grp_g2_exact<kTestThreads>(spec, T, M, red, table_out);
+    const double st = stat == kStatX2 ? grp_x2_exact<kTestThreads>(spec, T, M, red, table_out)
+                                      : grp_g2_exact<kTestThreads>(spec, T, M, red, table_out);
+    const double df = df_mode ? (double)grp_df_adjusted<kTestThreads>(spec, M, red)
+                              : (double)(spec.rx - 1) * (double)(spec.ry - 1) * (double)(spec.cells / (spec.rx * spec.ry));
     if (threadIdx.x == 0) {
-        const double df = (double)(spec.rx - 1) * (double)(spec.ry - 1) * (double)(spec.cells / (spec.rx * spec.ry));
-        out[3 * t + 0] = g2;
+        out[3 * t + 0] = st;
         out[3 * t + 1] = df;
-        out[3 * t + 2] = chisq_q(df, g2, status);
+        out[3 * t + 2] = df > 0.0 ? chisq_q(df, st, status) : 1.0;
     }
 }
 
@@ -840,10 +848,11 @@ void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsig
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
-                     size_t smem_bytes, cudaStream_t st)
+                     size_t smem_bytes, int stat, int df_mode, cudaStream_t st)
 {
     k_ci_tests<<<ntests, kTestThreads, smem_bytes, st>>>(prob, tests, ntests, out, table_out, gscratch,
-                                                         gscratch_ints, status, (int)(smem_bytes / 4));
+                                                         gscratch_ints, status, (int)(smem_bytes / 4), stat,
+                                                         df_mode);
 }
 
 cudaError_t set_kernel_smem(size_t max_smem)

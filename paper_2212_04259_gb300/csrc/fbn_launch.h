@@ -36,7 +36,7 @@ void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsig
                       unsigned long long* cursor, cudaStream_t st);
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
-                     size_t smem_bytes, cudaStream_t st);
+                     size_t smem_bytes, int stat, int df_mode, cudaStream_t st);
 cudaError_t set_kernel_smem(size_t max_smem);
 // Sets the message fbn_last_error(NULL) returns.
 void fbn_internal_set_error(const char* msg);
