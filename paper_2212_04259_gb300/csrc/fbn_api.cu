@@ -23,7 +23,7 @@ namespace {
 
 thread_local std::string g_create_error;
 
-constexpr size_t kSmemBytes = 108 * 1024;     // dynamic shared memory of a CTA test group (2 CTAs / SM)
+constexpr size_t kSmemBytes = 100 * 1024;     // dynamic shared memory of a CTA test group: 2 CTAs / SM with the ~9 KB static
 constexpr long long kSplitStride = 4096;        // cells of a split test's global table at most
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
