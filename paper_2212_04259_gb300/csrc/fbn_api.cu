@@ -719,8 +719,20 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     // The kernels of one depth after the edge list: ordering + pool per class,
     // then removal and the end of the depth.
     auto enqueue_tests = [&](bool big_possible) -> int {
-        for (int cls = 0; cls < 2; ++cls) {
-            if (cls == kClassCta && !big_possible) continue;
+        const int nclass = big_possible ? 2 : 1;
+        if (!plain) {   // both classes ordered up front: their sorted orders do not overlap
+            ScanClass sc[2];
+            for (int cls = 0; cls < 2; ++cls) {
+                sc[cls].hist = ws.hist + cls * ws.ord_cap;
+                sc[cls].alive = ws.alive + cls * ws.ord_cap;
+                sc[cls].base = ws.base + cls * ws.ord_cap;
+                for (int k = 0; k < 4; ++k) sc[cls].groups[k] = cls == 0 ? groups[k] : groups_big[k];
+                sc[cls].smem_ints = (long long)((cls == 0 ? kWarpSmemBytes : kSmemBytes) / 4);
+            }
+            launch_order(ws.edges, ws.edge_cap, nclass, ws.d_ctr, sc, ws.cursor, ws.cursor + ws.ord_cap, ws.sorted,
+                         mean_n, forced, kSplitStride, 1, grid_aux, st);
+        }
+        for (int cls = 0; cls < nclass; ++cls) {
             PoolArgs a = base;
             a.cls = cls;
             const bool small = cls == kClassWarp && !plain;
@@ -734,17 +746,11 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
                 launch_plain(a, grid_big, kSmemBytes, st);
                 continue;
             }
-            unsigned long long* cls_base = ws.base + cls * ws.ord_cap;
-            a.base = cls_base;
+            a.base = ws.base + cls * ws.ord_cap;
             a.sorted = ws.sorted;
-            // the two classes share the sorted array: the next class's ordering
-            // runs after this pool on the same stream
-            launch_order(ws.edges, ws.edge_cap, cls, ws.d_ctr, ws.hist + cls * ws.ord_cap, ws.alive + cls * ws.ord_cap,
-                         cls_base, ws.cursor + cls * ws.ord_cap, ws.sorted, small ? groups : groups_big, mean_n,
-                         forced, (long long)(smem / 4), kSplitStride, 1, grid_aux, st);
             launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
         }
-        return plain ? (big_possible ? 2 : 1) : (big_possible ? 6 : 3);
+        return plain ? nclass : 2 + nclass;
     };
     auto enqueue_head = [&]() {
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
@@ -844,7 +850,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         } else {
             const bool big = big_at(d);
             CK(cudaGraphLaunch(ws.graph[par][big ? 1 : 0], st));
-            launches += 4 + (plain ? (big ? 2 : 1) : (big ? 6 : 3));
+            launches += 4 + (plain ? (big ? 2 : 1) : (big ? 4 : 3));
         }
         CK(cudaGetLastError());
         queued = d + 1;

@@ -119,6 +119,15 @@ __host__ __device__ __forceinline__ long long chunk_count(long long total, int g
     return (total + c - 1) / c;
 }
 
+// Per-class arguments of the ordering scan.
+struct ScanClass {
+    const unsigned long long* hist;   // chunk-count histogram of the class
+    unsigned long long* alive;        // [maxc + 1] edges with more than k chunks
+    unsigned long long* base;         // [maxc + 1] first item of pass k
+    long long groups[4];              // groups of 32, 64, 128, 256 threads the class's pool runs
+    long long smem_ints;              // shared ints of one pool CTA of the class
+};
+
 // Cache of critical values, see fbn_device.cuh.
 struct CritTableDev {
     long long* keys;

@@ -228,14 +228,19 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
 constexpr double kTestOverhead = 10000.0;
 constexpr double kCyclesPerSample = 8.0;
 
-__global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, DepthCounters* ctr,
-                       unsigned long long* __restrict__ alive, unsigned long long* __restrict__ base,
-                       long long g32, long long g64, long long g128, long long g256, double mean_n,
-                       int forced_group, long long smem_ints, long long split_stride, int allow_split)
+__global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double mean_n, int forced_group,
+                       long long split_stride, int allow_split)
 {
     pdl_enter();
     __shared__ unsigned long long sh[32];
     if (!ctr->active) return;
+    const int cls = blockIdx.x;   // one CTA per edge class
+    const ScanClass& sc = cls == 0 ? c0 : c1;
+    const unsigned long long* __restrict__ hist = sc.hist;
+    unsigned long long* __restrict__ alive = sc.alive;
+    unsigned long long* __restrict__ base = sc.base;
+    const long long g32 = sc.groups[0], g64 = sc.groups[1], g128 = sc.groups[2], g256 = sc.groups[3];
+    const long long smem_ints = sc.smem_ints;
     const long long maxc = (long long)ctr->maxc[cls];
     if (ctr->n_edges[cls] == 0) return;
     const int T = blockDim.x;
@@ -303,19 +308,27 @@ __global__ void k_scan(const unsigned long long* __restrict__ hist, int cls, Dep
     }
 }
 
-__global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, int cls,
-                        const DepthCounters* ctr, const unsigned long long* __restrict__ alive,
-                        unsigned long long* __restrict__ cursor, int32_t* __restrict__ sorted)
+// Both classes at once: class c's order goes to sorted[class_base(c) ..], the
+// same region its edges occupy, so the two never overlap.
+__global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, int nclass,
+                        const DepthCounters* ctr, const unsigned long long* __restrict__ alive0,
+                        unsigned long long* __restrict__ cursor0, const unsigned long long* __restrict__ alive1,
+                        unsigned long long* __restrict__ cursor1, int32_t* __restrict__ sorted)
 {
     pdl_enter();
     if (!ctr->active) return;
     const int gs = ctr->gs;
-    const long long E = (long long)ctr->n_edges[cls];
-    const EdgeWork* ed = edges + class_base(ctr, cls, edge_cap);
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
-        const long long ch = chunk_count(ed[e].total, gs);
-        const unsigned long long pos = alive[ch] + atomicAdd(&cursor[ch], 1ULL);
-        sorted[pos] = (int32_t)e;
+    const long long E0 = (long long)ctr->n_edges[0];
+    const long long E = E0 + (nclass > 1 ? (long long)ctr->n_edges[1] : 0);
+    const long long b1 = class_base(ctr, 1, edge_cap);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < E; k += (long long)gridDim.x * blockDim.x) {
+        const bool first = k < E0;
+        const long long e = first ? k : k - E0;
+        const long long cb = first ? 0 : b1;
+        const long long ch = chunk_count(edges[cb + e].total, gs);
+        const unsigned long long pos =
+            first ? alive0[ch] + atomicAdd(&cursor0[ch], 1ULL) : alive1[ch] + atomicAdd(&cursor1[ch], 1ULL);
+        sorted[cb + (long long)pos] = (int32_t)e;
     }
 }
 
@@ -530,7 +543,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
                     const long long mid = (lo + hi + 1) >> 1;
                     if (base[mid] <= w) lo = mid; else hi = mid - 1;
                 }
-                const int e = a.sorted[w - base[lo]];
+                const int e = a.sorted[cb + (long long)(w - base[lo])];
                 const long long tot = edges[e].total;
                 const long long cr = chunk_ranks(tot, gs);
                 const long long r0 = lo * cr;
@@ -680,7 +693,9 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
                             unsigned long long* cursor)
 {
     pdl_enter();
+    __shared__ long long used[2];   // histogram / cursor entries this depth touched per class
     if (!ctr->active) return;
+    if (threadIdx.x < 2) used[threadIdx.x] = (long long)ctr->maxc[threadIdx.x] + 1;
     __syncthreads();
     if (threadIdx.x == 0) {
         const int d = ctr->d;
@@ -706,10 +721,14 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
         __threadfence();
         ctr->active = stop ? 0 : 1;
     }
-    const long long n = 2 * (kMaxPasses + 1);
-    for (long long k = threadIdx.x; k < n; k += blockDim.x) {
-        hist[k] = 0;
-        cursor[k] = 0;
+    for (int c = 0; c < 2; ++c) {
+        const long long n = used[c] < kMaxPasses + 1 ? used[c] : kMaxPasses + 1;
+        unsigned long long* hc = hist + c * (kMaxPasses + 1);
+        unsigned long long* cc = cursor + c * (kMaxPasses + 1);
+        for (long long k = threadIdx.x; k < n; k += blockDim.x) {
+            hc[k] = 0;
+            cc[k] = 0;
+        }
     }
 }
 
@@ -810,15 +829,14 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
                edge_cap, ctr, hist);
 }
 
-void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
-                  unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
-                  unsigned long long* cursor, int32_t* sorted, const long long groups[4], double mean_n,
-                  int forced_group, long long smem_ints, long long split_stride, int allow_split, int grid,
-                  cudaStream_t st)
+void launch_order(const EdgeWork* edges, long long edge_cap, int nclass, DepthCounters* ctr, const ScanClass* sc,
+                  unsigned long long* cursor0, unsigned long long* cursor1, int32_t* sorted, double mean_n,
+                  int forced_group, long long split_stride, int allow_split, int grid, cudaStream_t st)
 {
-    launch_pdl(k_scan, dim3(1), dim3(1024), 0, st, hist, cls, ctr, alive, base, groups[0], groups[1], groups[2],
-               groups[3], mean_n, forced_group, smem_ints, split_stride, allow_split);
-    launch_pdl(k_place, dim3(grid), dim3(256), 0, st, edges, edge_cap, cls, ctr, alive, cursor, sorted);
+    launch_pdl(k_scan, dim3(nclass), dim3(1024), 0, st, sc[0], sc[nclass > 1 ? 1 : 0], ctr, mean_n, forced_group,
+               split_stride, allow_split);
+    launch_pdl(k_place, dim3(grid), dim3(256), 0, st, edges, edge_cap, nclass, ctr, (const unsigned long long*)sc[0].alive,
+               cursor0, (const unsigned long long*)sc[nclass > 1 ? 1 : 0].alive, cursor1, sorted);
 }
 
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st)

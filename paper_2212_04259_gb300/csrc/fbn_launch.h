@@ -22,11 +22,11 @@ void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_
                   long long warp_cells_cap,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st);
-void launch_order(const EdgeWork* edges, long long edge_cap, int cls, DepthCounters* ctr,
-                  unsigned long long* hist, unsigned long long* alive, unsigned long long* base,
-                  unsigned long long* cursor, int32_t* sorted, const long long groups[4], double mean_n,
-                  int forced_group, long long smem_ints, long long split_stride, int allow_split, int grid,
-                  cudaStream_t st);
+// Ordering of the depth's edges, one CTA per class (nclass = 1: the small-
+// table class only), then the placement of both classes.
+void launch_order(const EdgeWork* edges, long long edge_cap, int nclass, DepthCounters* ctr, const ScanClass* sc,
+                  unsigned long long* cursor0, unsigned long long* cursor1, int32_t* sorted, double mean_n,
+                  int forced_group, long long split_stride, int allow_split, int grid, cudaStream_t st);
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
