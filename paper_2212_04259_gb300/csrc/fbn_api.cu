@@ -489,10 +489,11 @@ int prepare_gram(fbn_handle* const* hs, int k, Workspace& ws, ProblemDev* P)
         P[p].onehot_ld = q->K;
         P[p].gram_ld = q->Mp;
         CK(encode_onehot_map(ws.h_maps.data() + p * mb, P[p].onehot, q->Mp, q->K));
-        const int T = q->Mp / 128, C = gram_chunks(q->K);
+        // 128-row tiles a against 256-row tiles b that reach the upper triangle
+        const int T = q->Mp / 128, T2 = (T + 1) / 2, C = gram_chunks(q->K);
         for (int c = 0; c < C; ++c)
             for (int a = 0; a < T; ++a)
-                for (int b = a; b < T; ++b) units.push_back(make_int4(p, a, b, c));
+                for (int b = a / 2; b < T2; ++b) units.push_back(make_int4(p, a, b, c));
         eo += (long long)q->Mp * q->K;
         go += (long long)q->Mp * q->Mp;
     }

@@ -11,11 +11,14 @@
 // tcgen05.mma.kind::f8f6f4 with FP32 accumulators in tensor memory; every
 // accumulation covers at most kChunk = 8192 samples, so each partial sum is an
 // integer below 2^13 and exact even if the accumulation kept only 14
-// significant bits.  Each chunk's 128x128 tile is added into an INT32 Gram in
+// significant bits.  Each chunk's 128x256 tile is added into an INT32 Gram in
 // global memory.  (tcgen05.mma.kind::i8 does not assemble for sm_103a with this
 // toolkit, hence FP8 0/1 operands.)
 //
-// Work unit = (upper-triangle tile pair, chunk of samples), chunk-major so
+// A tile is 128 rows of E against 256 rows (M = 128, N = 256 per MMA): each
+// 128-sample stage brings 48 KB of operands for 8 MFLOP, a third less operand
+// traffic per FLOP than square 128-row tiles.  Work unit = (128-row tile,
+// 256-row tile reaching the upper triangle, chunk of samples), chunk-major so
 // that the CTAs of a wave stream the same sample range and share it in L2.
 // CTA roles: warps 0-3 epilogue (TMEM -> registers -> coalesced INT32 atomic
 // adds), warp 4 TMA producer, warp 5 MMA issuer and TMEM owner.
@@ -35,21 +38,23 @@ namespace {
 
 using namespace tc;
 
-constexpr int kTile = 128;                           // rows of a tile = M = N of one MMA
+constexpr int kTile = 128;                           // rows of an A tile = M of one MMA
+constexpr int kTileN = 256;                          // rows of a B tile = N of one MMA
 constexpr int kKSlice = 128;                         // samples (bytes) per pipeline stage
 constexpr int kChunk = 8192;                         // samples per exact accumulation
 constexpr int kSlicesPerChunk = kChunk / kKSlice;
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kTileBytes = kTile * kKSlice;          // 16 KB
-constexpr int kStageBytes = 2 * kTileBytes;          // A + B
+constexpr int kStageBytes = 3 * kTileBytes;          // A + the two 128-row halves of B
 constexpr int kGramThreads = 192;
-constexpr uint32_t kTmemCols = 256;                  // two 128-column FP32 accumulators
+constexpr uint32_t kTmemCols = 512;                  // two 256-column FP32 accumulators
 constexpr int kStagePad = 33;                        // epilogue transpose tile row (ints)
 constexpr size_t kGramSmem = 1024 /*align*/ + (size_t)kStages * kStageBytes + 4 * 32 * kStagePad * 4 + 256;
 
-constexpr uint32_t kIdesc = tc::idesc_f8(kTile, kTile);
+constexpr uint32_t kIdesc = tc::idesc_f8(kTile, kTileN);
 
-// Work unit of the Gram: problem, tile pair (ti <= tj), chunk of samples.
+// Work unit of the Gram: problem, 128-row tile ti, 256-row tile tj covering
+// some column >= some row (tj >= ti / 2), chunk of samples.
 struct GramArgs {
     const CUtensorMap* maps;    // [problems] tensor maps of the one-hot matrices (global memory)
     const int4* units;          // [n_units] (problem, ti, tj, chunk)
@@ -124,7 +129,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
                     const uint32_t a = smem_u32(smem + (size_t)stage * kStageBytes);
                     mbar_expect_tx(fb, kStageBytes);
                     tma_load_2d(a, map, fb, kb * kKSlice, t.y * kTile);
-                    tma_load_2d(a + kTileBytes, map, fb, kb * kKSlice, t.z * kTile);
+                    // B: rows beyond the padded matrix (odd tile count) come back as zeros
+                    tma_load_2d(a + kTileBytes, map, fb, kb * kKSlice, t.z * kTileN);
+                    tma_load_2d(a + 2 * kTileBytes, map, fb, kb * kKSlice, t.z * kTileN + kTile);
                     issued[stage] += 1;
                     if (++stage == kStages) {
                         stage = 0;
@@ -148,7 +155,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
                 const int kb1 = min(kb0 + kSlicesPerChunk, slices);
                 if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag, g.status, g.limit)) break;
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * kTile);
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * kTileN);
                 for (int kb = kb0; kb < kb1; ++kb) {
                     if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag, g.status, g.limit)) {
                         ok = false;
@@ -188,15 +195,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_gram(GramArgs g)
             const long long ldg = g.probs[t.x].gram_ld;
             if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag, g.status, g.limit)) break;
             tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kTile);
+            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kTileN);
             const long long row0 = (long long)t.y * kTile + warp * 32;
-            for (int j0 = 0; j0 < kTile; j0 += 32) {
+            for (int j0 = 0; j0 < kTileN; j0 += 32) {
+                if ((long long)t.z * kTileN + j0 >= ldg) break;   // columns past the padded matrix
                 uint32_t v[32];
                 tmem_ld32(base + (uint32_t)j0, v);
 #pragma unroll
                 for (int q = 0; q < 32; ++q) xp[lane * kStagePad + q] = __float2int_rn(__uint_as_float(v[q]));
                 __syncwarp();
-                int32_t* dst = G + row0 * ldg + (long long)t.z * kTile + j0 + lane;
+                int32_t* dst = G + row0 * ldg + (long long)t.z * kTileN + j0 + lane;
 #pragma unroll 4
                 for (int r = 0; r < 32; ++r) {
                     const int val = xp[r * kStagePad + lane];
