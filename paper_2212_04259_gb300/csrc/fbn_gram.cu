@@ -279,6 +279,23 @@ __global__ void k_onehot(const ProblemDev* __restrict__ probs, const int32_t* __
     }
 }
 
+// Critical values of df <= kCritLocal, cached per CTA in shared memory (NaN
+// until first asked): the pairs of a depth share a handful of df, and the
+// global cache's acquire loads would serialise on those few slots.
+constexpr int kCritLocal = 64;
+
+__device__ __forceinline__ double crit_local(double* local, const CritTableDev& crit, long long df, double alpha,
+                                             unsigned* status)
+{
+    if (df > kCritLocal) return crit_get(crit, df, alpha, status);
+    double c = *((volatile double*)&local[df]);
+    if (c != c) {   // not cached yet: every thread that misses stores the same value
+        c = crit_get(crit, df, alpha, status);
+        *((volatile double*)&local[df]) = c;
+    }
+    return c;
+}
+
 // Decision of one depth-0 pair from its block of the Gram (row sums, column
 // sums and the total from the block itself).  R bounds the arities so that
 // the sums live in registers.  stat: G^2 or Pearson X^2; df_mode: declared
@@ -286,7 +303,7 @@ __global__ void k_onehot(const ProblemDev* __restrict__ probs, const int32_t* __
 template <int R>
 __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, int rx, int ry, long long e,
                                               unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                              double alpha, DepthCounters* ctr, int stat, int df_mode)
+                                              double alpha, DepthCounters* ctr, int stat, int df_mode, double* local)
 {
     int rs[R], cs[R];
     int tot = 0;
@@ -318,7 +335,7 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
     }
     // terms in FP32 (G^2: within 3.2e-7 of their magnitude; X^2: within 6e-7)
     // summed in FP64; exact FP64 only when crit lies inside the error band
-    const double c = crit_get(crit, df, alpha, &ctr->status);
+    const double c = crit_local(local, crit, df, alpha, &ctr->status);
     double acc = 0.0, mag = 0.0;
 #pragma unroll
     for (int x = 0; x < R; ++x)
@@ -377,7 +394,7 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
 // the statistic in FP64.
 __device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp, int rx, int ry, long long e,
                                                  unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                                 double alpha, DepthCounters* ctr, int stat, int df_mode)
+                                                 double alpha, DepthCounters* ctr, int stat, int df_mode, double* local)
 {
     long long tot = 0;
     for (int x = 0; x < rx; ++x)
@@ -401,7 +418,7 @@ __device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp,
         min_accept[e] = 0;
         return;
     }
-    const double c = crit_get(crit, df, alpha, &ctr->status);
+    const double c = crit_local(local, crit, df, alpha, &ctr->status);
     double ex = 0.0;
     for (int x = 0; x < rx; ++x) {
         long long rsx = 0;
@@ -427,16 +444,16 @@ __device__ __forceinline__ void pair_decide_wide(const int32_t* T, long long Mp,
 __device__ __forceinline__ void pair_decide(const EdgeWork* __restrict__ edges, long long e,
                                             const ProblemDev* __restrict__ probs,
                                             unsigned long long* __restrict__ min_accept, const CritTableDev& crit,
-                                            double alpha, DepthCounters* ctr, int stat, int df_mode)
+                                            double alpha, DepthCounters* ctr, int stat, int df_mode, double* local)
 {
     const EdgeWork w = edges[e];
     const ProblemDev& P = probs[w.prob];
     const int rx = P.ar[w.i], ry = P.ar[w.j];
     const long long Mp = P.gram_ld;
     const int32_t* T = P.gram + (long long)P.off[w.i] * Mp + P.off[w.j];
-    if (rx <= 4 && ry <= 4) pair_decide_r<4>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
-    else if (rx <= 8 && ry <= 8) pair_decide_r<8>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
-    else pair_decide_wide(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode);
+    if (rx <= 4 && ry <= 4) pair_decide_r<4>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode, local);
+    else if (rx <= 8 && ry <= 8) pair_decide_r<8>(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode, local);
+    else pair_decide_wide(T, Mp, rx, ry, e, min_accept, crit, alpha, ctr, stat, df_mode, local);
 }
 
 // Depth-0 decisions from the Gram: one thread per edge (i<j) of both classes
@@ -445,12 +462,15 @@ __global__ void k_pairs_decide(const EdgeWork* __restrict__ edges, long long edg
                                const ProblemDev* __restrict__ probs, unsigned long long* __restrict__ min_accept,
                                CritTableDev crit, double alpha, DepthCounters* ctr, int stat, int df_mode)
 {
+    __shared__ double local[kCritLocal + 1];
     if (!ctr->active) return;
+    for (int k = threadIdx.x; k <= kCritLocal; k += blockDim.x) local[k] = __longlong_as_double(0x7ff8000000000000LL);
+    __syncthreads();
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
          k += (long long)gridDim.x * blockDim.x)
         pair_decide(edges, k < n0 ? k : edge_cap - n1 + (k - n0), probs, min_accept, crit, alpha, ctr, stat,
-                    df_mode);
+                    df_mode, local);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctr->tests, (unsigned long long)(n0 + n1));   // one test per pair
 }
 // Zero the pad rows M..Mp of every problem's one-hot matrix (one CTA per
