@@ -126,6 +126,9 @@ struct Workspace {
     size_t h_up_cap = 0;
     int gram_n_units = 0;
     std::vector<uint8_t> h_maps;
+    // one-hot layout of the last prepare_gram and the last one whose pad rows
+    // were zeroed (k_onehot writes only the rows below M)
+    std::vector<long long> gram_layout, gram_zeroed;
     // CUDA graphs of one generic depth: [parity][big-table class queued]
     cudaGraphExec_t graph[2][2] = {};
     std::vector<uint8_t> graph_key;
@@ -193,6 +196,7 @@ struct fbn_handle {
     uint8_t* d_adj = nullptr;
     int32_t* d_nbr = nullptr;
     int32_t* d_eid = nullptr;
+    int32_t* d_npos = nullptr;
     int32_t* d_deg = nullptr;
     int32_t* d_sep_len = nullptr;
     int64_t* d_sep_off = nullptr;
@@ -481,6 +485,7 @@ int prepare_gram(fbn_handle* const* hs, int k, Workspace& ws, ProblemDev* P)
     ws.h_maps.assign(k * mb, 0);
     std::vector<int4> units;
     long long eo = 0, go = 0;
+    ws.gram_layout.assign(1, (long long)(uintptr_t)ws.gram_E);
     for (int p = 0; p < k; ++p) {
         const fbn_handle* q = hs[p];
         P[p].off = q->d_off;
@@ -494,6 +499,10 @@ int prepare_gram(fbn_handle* const* hs, int k, Workspace& ws, ProblemDev* P)
         for (int c = 0; c < C; ++c)
             for (int a = 0; a < T; ++a)
                 for (int b = a / 2; b < T2; ++b) units.push_back(make_int4(p, a, b, c));
+        ws.gram_layout.push_back(eo);
+        ws.gram_layout.push_back(q->M);
+        ws.gram_layout.push_back(q->Mp);
+        ws.gram_layout.push_back(q->K);
         eo += (long long)q->Mp * q->K;
         go += (long long)q->Mp * q->Mp;
     }
@@ -518,7 +527,10 @@ int run_gram(fbn_handle* h, Workspace& ws, int k, int total_vtx, unsigned* d_sta
     cudaStream_t st = h->stream;
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
-    CK(launch_zero_pad(ws.probs, k, st));
+    if (ws.gram_layout != ws.gram_zeroed) {   // pad rows stay zero while the layout holds
+        CK(launch_zero_pad(ws.probs, k, st));
+        ws.gram_zeroed = ws.gram_layout;
+    }
     CK(launch_onehot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, st));
     CK(cudaMemsetAsync(ws.gram_G, 0, ws.gram_G_cap * sizeof(int32_t), st));
     if (ev0) CK(cudaEventRecord(ev0, st));
@@ -603,7 +615,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         total_vtx += q->n;
         for (int v = 0; v < q->n; ++v) vtx_prob.push_back(p);
         ProblemDev& d = P[p];
-        d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.eid = q->d_eid; d.deg = q->d_deg;
+        d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.eid = q->d_eid; d.npos = q->d_npos; d.deg = q->d_deg;
         d.sep_len = q->d_sep_len; d.sep_off = q->d_sep_off; d.ld = q->ld; d.n = q->n; d.N = (int32_t)q->N;
         d.max_arity = q->max_arity; d.pad = 0;
     }
@@ -1019,7 +1031,7 @@ void free_handle(fbn_handle* h)
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     h->ws.release();
-    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_deg);
+    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
     dfree(h->d_off);
@@ -1121,6 +1133,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     CKC(dalloc(&h->d_adj, nn));
     CKC(dalloc(&h->d_nbr, nn));
     CKC(dalloc(&h->d_eid, nn));
+    CKC(dalloc(&h->d_npos, nn));
     CKC(dalloc(&h->d_deg, n_vars));
     CKC(dalloc(&h->d_sep_len, nn));
     CKC(dalloc(&h->d_sep_off, nn));
@@ -1168,7 +1181,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         CKC(cudaMemcpy(h->d_off, off.data(), n_vars * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     ProblemDev P{};
-    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.deg = h->d_deg;
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.npos = h->d_npos; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = n_vars; P.N = (int32_t)n_samples;
     P.max_arity = max_ar;
     CKC(cudaMemcpyAsync(h->d_prob, &P, sizeof P, cudaMemcpyHostToDevice, st));
@@ -1282,7 +1295,7 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)
     int rc = grow_workspace(h, ws, (long long)h->n * (h->n - 1) / 2, h->n, 1, h->n);
     if (rc) return rc;
     ProblemDev P{};
-    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.deg = h->d_deg;
+    P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.npos = h->d_npos; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = h->n; P.N = (int32_t)h->N;
     P.max_arity = h->max_arity;
     rc = prepare_gram(hs, 1, ws, &P);

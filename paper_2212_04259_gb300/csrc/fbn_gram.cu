@@ -333,10 +333,12 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
         min_accept[e] = 0;
         return;
     }
-    // terms in FP32 (G^2: within 3.2e-7 of their magnitude; X^2: within 6e-7)
-    // summed in FP64; exact FP64 only when crit lies inside the error band
+    // terms in FP32 (G^2: within 3.2e-7 of their magnitude; X^2: within 6e-7),
+    // summed in FP32 by this thread (at most R*R additions, each within 6e-8 of
+    // the running sum of magnitudes); exact FP64 only when crit lies inside the
+    // error band
     const double c = crit_local(local, crit, df, alpha, &ctr->status);
-    double acc = 0.0, mag = 0.0;
+    float acc = 0.0f, mag = 0.0f;
 #pragma unroll
     for (int x = 0; x < R; ++x)
 #pragma unroll
@@ -347,21 +349,23 @@ __device__ __forceinline__ void pair_decide_r(const int32_t* T, long long Mp, in
                 if (rs[x] == 0 || cs[y] == 0) continue;
                 const float fd = (float)((long long)n * tot - (long long)rs[x] * cs[y]);
                 const float t = fd * fd / ((float)tot * (float)rs[x] * (float)cs[y]);
-                acc += (double)t;
-                mag += (double)t;
+                acc += t;
+                mag += t;
             } else {
                 if (n == 0) continue;
                 const long long a = (long long)n * tot, b = (long long)rs[x] * cs[y];
                 const float fb = (float)b;
                 const float delta = (float)(a - b) / fb;
                 const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
-                acc += (double)((float)n * L);
-                mag += fabs((double)((float)n * L));
+                const float t = (float)n * L;
+                acc += t;
+                mag += fabsf(t);
             }
         }
     const double scale = stat == kStatX2 ? 1.0 : 2.0;
-    const double st = scale * acc;
-    const double err = scale * 2.0 * (stat == kStatX2 ? 6e-7 : 3.2e-7) * mag * 1.0001 + 1e-9;
+    const double st = scale * (double)acc;
+    const double rel = 2.0 * ((stat == kStatX2 ? 6e-7 : 3.2e-7) + (double)(rx * ry) * 6e-8);
+    const double err = scale * rel * (double)mag * 1.0001 + 1e-9;
     bool accept;
     if (st + err < c) {
         accept = true;

@@ -46,6 +46,7 @@ struct ProblemDev {
     int64_t onehot_ld;     // padded samples (multiple of 128)
     int64_t gram_ld;       // padded rows Mp (multiple of 128)
     int32_t* eid;          // [n][n] edge of the current depth at each snapshot slot nbr[v][t]
+    int32_t* npos;         // [n][n] npos[v][u] = index of u in nbr[v] (u adjacent to v in the snapshot)
     uint8_t* pk;           // [n][pk_ld] samples 4 bits each (depth-1 tensor-core path; arities <= 8)
     int64_t pk_ld;         // ld / 2
 };

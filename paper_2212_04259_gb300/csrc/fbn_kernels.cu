@@ -60,7 +60,11 @@ __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* 
         const int j = j0 + lane;
         const bool a = j < P.n && row[j];
         const unsigned m = __ballot_sync(0xffffffffu, a);
-        if (a) out[count + __popc(m & ((1u << lane) - 1u))] = j;
+        if (a) {
+            const int slot = count + __popc(m & ((1u << lane) - 1u));
+            out[slot] = j;
+            P.npos[(long long)v * P.n + j] = slot;
+        }
         count += __popc(m);
     }
     if (lane == 0) {
@@ -140,13 +144,7 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
                 continue;
             }
             const long long e = c == kClassWarp ? k : edge_cap - 1 - k;
-            // position of i in a(j)
-            const int32_t* nj = P.nbr + (long long)j * P.n;
-            int lo = 0, hi = P.deg[j];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (nj[mid] < i) lo = mid + 1; else hi = mid;
-            }
+            const int lo = P.npos[(long long)j * P.n + i];   // position of i in a(j)
             EdgeWork w;
             w.prob = p; w.i = i; w.j = j;
             w.posj = (int16_t)t; w.posi = (int16_t)lo;
