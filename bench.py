@@ -465,13 +465,15 @@ def main():
         host = torch.from_numpy(w["data"]).pin_memory()
         n = w["data"].shape[0]
         adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
-        he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local, depth1=args.depth1, statistic=args.statistic, df=args.df)
+        he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local, depth1=args.depth1,
+                          statistic=args.statistic, df=args.df)
         F.fbn_set_stream(he, stream)
         hs_e2e, hosts, adjs_host = [he], [host], [adj_host]
     else:
         hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
         adjs_host = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8).pin_memory() for d, _ in w["probs"]]
-        hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local, depth1=args.depth1, statistic=args.statistic, df=args.df)
+        hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local, depth1=args.depth1,
+                               statistic=args.statistic, df=args.df)
                   for hh, (_, a) in zip(hosts, w["probs"])]
         F.fbn_set_stream(hs_e2e[0], stream)
     e2e_ms, d2h = [], 0
