@@ -15,6 +15,7 @@
 #include "../../include/fbn.h"
 #include "fbn_gram.h"
 #include "fbn_nbr.h"
+#include "fbn_sepsets.h"
 #include "fbn_launch.h"
 
 using namespace fbn;
@@ -174,8 +175,6 @@ struct Workspace {
 struct DeviceInts {
     int32_t* d = nullptr;
     long long n = 0;
-    std::vector<int32_t> host;   // host copy, made by the first handle that asks
-    bool host_ready = false;
     ~DeviceInts()
     {
         if (d) cudaFree(d);
@@ -224,9 +223,17 @@ struct fbn_handle {
     // members of a batch's separating sets: a device copy of the batch's
     // shared pool, held by every handle of that batch until it learns again
     std::shared_ptr<DeviceInts> sep_snap;
-    std::vector<int32_t> sep_len;      // n*n, i<j entries
-    std::vector<int64_t> sep_off;      // n*n offsets into sep_members
-    std::vector<int32_t> sep_members;
+    // separating sets on the host, CSR: removed pairs (i < j) ascending, their
+    // member offsets (one more than pairs), the members
+    std::vector<int32_t> csr_pairs;
+    std::vector<int64_t> csr_offs;
+    std::vector<int32_t> csr_members;
+    // device side of the compaction, grown as needed
+    long long* d_sep_cnt = nullptr;     // [2n] row counts, then [2][n + 1] row offsets
+    int32_t* d_csr_pairs = nullptr;
+    int64_t* d_csr_offs = nullptr;
+    int32_t* d_csr_members = nullptr;
+    long long csr_pairs_cap = 0, csr_members_cap = 0;
     fbn_stats stats{};
     Workspace ws;
     std::string err;
@@ -537,47 +544,67 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
     if (!h->sep_pending) return FBN_OK;
     CK(cudaSetDevice(h->device));
     cudaStream_t st = h->stream;
-    const size_t nn = (size_t)h->n * h->n;
-    // the members: this handle's own pool, or the batch's snapshot, copied
-    // to the host once for the whole batch
-    std::vector<int32_t> own;
-    const int32_t* pool = nullptr;
-    DeviceInts* snap = h->sep_snap.get();
-    if (snap) {
-        if (!snap->host_ready) {
-            snap->host.resize(h->sep_pool_used);
-            if (h->sep_pool_used)
-                CK(cudaMemcpyAsync(snap->host.data(), snap->d, h->sep_pool_used * sizeof(int32_t),
-                                   cudaMemcpyDeviceToHost, st));
-            snap->host_ready = true;
-        }
-        pool = snap->host.data();
-    } else {
-        own.resize(h->sep_pool_used);
-        if (h->sep_pool_used)
-            CK(cudaMemcpyAsync(own.data(), ws.sep_pool, h->sep_pool_used * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                               st));
-        pool = own.data();
-    }
-    std::vector<int32_t> len(nn);
-    std::vector<int64_t> off(nn);
-    CK(cudaMemcpyAsync(len.data(), h->d_sep_len, nn * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(off.data(), h->d_sep_off, nn * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    const int n = h->n;
+    // the members live in this handle's pool, or in its batch's snapshot
+    const int32_t* pool = h->sep_snap ? h->sep_snap->d : ws.sep_pool;
+    if (!h->d_sep_cnt) CK(dalloc(&h->d_sep_cnt, 4 * (size_t)n + 4));
+    long long* cnt = h->d_sep_cnt;
+    long long* roff_p = cnt + 2 * (size_t)n;
+    long long* roff_m = roff_p + n + 1;
+    CK(launch_sep_count(h->d_sep_len, n, cnt, roff_p, roff_m, st));
+    long long tot[2] = {0, 0};
+    CK(cudaMemcpyAsync(&tot[0], roff_p + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&tot[1], roff_m + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    h->sep_len.assign(nn, -1);
-    h->sep_off.assign(nn, 0);
-    h->sep_members.clear();
-    for (int i = 0; i < h->n; ++i)
-        for (int j = i + 1; j < h->n; ++j) {
-            const size_t ij = (size_t)i * h->n + j;
-            const int32_t L = len[ij];
-            if (L < 0) continue;
-            h->sep_len[ij] = L;
-            h->sep_off[ij] = (int64_t)h->sep_members.size();
-            for (int t = 0; t < L; ++t) h->sep_members.push_back(pool[(size_t)off[ij] + t]);
-        }
+    const long long R = tot[0], Mtot = tot[1];
+    if (R > h->csr_pairs_cap) {
+        dfree(h->d_csr_pairs);
+        dfree(h->d_csr_offs);
+        h->d_csr_pairs = nullptr;
+        h->d_csr_offs = nullptr;
+        h->csr_pairs_cap = 0;
+        CK(dalloc(&h->d_csr_pairs, 2 * (size_t)R));
+        CK(dalloc(&h->d_csr_offs, (size_t)R + 1));
+        h->csr_pairs_cap = R;
+    }
+    if (Mtot > h->csr_members_cap) {
+        dfree(h->d_csr_members);
+        h->d_csr_members = nullptr;
+        h->csr_members_cap = 0;
+        CK(dalloc(&h->d_csr_members, (size_t)Mtot));
+        h->csr_members_cap = Mtot;
+    }
+    h->csr_pairs.resize(2 * (size_t)R);
+    h->csr_offs.resize((size_t)R + 1);
+    h->csr_members.resize((size_t)Mtot);
+    if (R > 0) {
+        CK(launch_sep_write(h->d_sep_len, h->d_sep_off, pool, n, roff_p, roff_m, h->d_csr_pairs, h->d_csr_offs,
+                            h->d_csr_members, st));
+        CK(cudaMemcpyAsync(h->csr_pairs.data(), h->d_csr_pairs, 2 * (size_t)R * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(h->csr_offs.data(), h->d_csr_offs, (size_t)R * sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           st));
+        if (Mtot > 0)
+            CK(cudaMemcpyAsync(h->csr_members.data(), h->d_csr_members, (size_t)Mtot * sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    h->csr_offs[(size_t)R] = Mtot;
     h->sep_pending = false;
     return FBN_OK;
+}
+
+// Index of the removed pair (i < j) in the handle's CSR, or -1.
+long long find_sepset(const fbn_handle* h, int i, int j)
+{
+    long long lo = 0, hi = (long long)h->csr_offs.size() - 1;   // pairs [0, R)
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        const int a = h->csr_pairs[2 * mid], b = h->csr_pairs[2 * mid + 1];
+        if (a < i || (a == i && b < j)) lo = mid + 1; else hi = mid;
+    }
+    if (lo < (long long)h->csr_offs.size() - 1 && h->csr_pairs[2 * lo] == i && h->csr_pairs[2 * lo + 1] == j) return lo;
+    return -1;
 }
 
 // The depth loop of Algorithm 1 over one or more problems sharing a stream,
@@ -1024,6 +1051,7 @@ void free_handle(fbn_handle* h)
     h->ws.release();
     dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
+    dfree(h->d_sep_cnt); dfree(h->d_csr_pairs); dfree(h->d_csr_offs); dfree(h->d_csr_members);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
     dfree(h->d_off);
     if (h->h_ci) cudaFreeHost(h->h_ci);
@@ -1317,11 +1345,11 @@ int32_t fbn_get_sepset(const fbn_handle* hc, int32_t i, int32_t j, int32_t* buf,
     }
     if (i < 0 || j < 0 || i >= h->n || j >= h->n || i == j) return FBN_EINVAL;
     if (i > j) std::swap(i, j);
-    const size_t ij = (size_t)i * h->n + j;
-    const int32_t L = h->sep_len[ij];
-    if (L < 0) return -1;
+    const long long k = find_sepset(h, i, j);
+    if (k < 0) return -1;
+    const int32_t L = (int32_t)(h->csr_offs[k + 1] - h->csr_offs[k]);
     if (L > 0 && cap > 0 && !buf) return FBN_EINVAL;
-    for (int t = 0; t < L && t < cap; ++t) buf[t] = h->sep_members[(size_t)h->sep_off[ij] + t];
+    for (int t = 0; t < L && t < cap; ++t) buf[t] = h->csr_members[(size_t)h->csr_offs[k] + t];
     return L;
 }
 
@@ -1334,19 +1362,10 @@ int fbn_export_sepsets(const fbn_handle* hc, int64_t* n_removed, int64_t* n_memb
         const int rc = materialize_sepsets(h, h->ws);
         if (rc) return rc;
     }
-    int64_t nr = 0, nm = 0;
-    for (int i = 0; i < h->n; ++i)
-        for (int j = i + 1; j < h->n; ++j) {
-            const size_t ij = (size_t)i * h->n + j;
-            const int32_t L = h->sep_len[ij];
-            if (L < 0) continue;
-            if (pairs) { pairs[2 * nr] = i; pairs[2 * nr + 1] = j; }
-            if (offsets) offsets[nr] = nm;
-            if (members)
-                for (int t = 0; t < L; ++t) members[nm + t] = h->sep_members[(size_t)h->sep_off[ij] + t];
-            ++nr;
-            nm += L;
-        }
+    const int64_t nr = (int64_t)h->csr_offs.size() - 1, nm = h->csr_offs.back();
+    if (pairs && nr > 0) std::memcpy(pairs, h->csr_pairs.data(), 2 * (size_t)nr * sizeof(int32_t));
+    if (offsets && nr > 0) std::memcpy(offsets, h->csr_offs.data(), (size_t)nr * sizeof(int64_t));
+    if (members && nm > 0) std::memcpy(members, h->csr_members.data(), (size_t)nm * sizeof(int32_t));
     if (offsets) offsets[nr] = nm;
     *n_removed = nr;
     *n_members = nm;
@@ -1373,10 +1392,10 @@ int fbn_orient_cpdag(const fbn_handle* hc, uint8_t* cpdag_out)
             if (A[(size_t)u * n + v]) nb[u].push_back(v);
     auto adj = [&](int u, int v) { return A[(size_t)u * n + v] != 0; };
     auto in_sepset = [&](int a, int b, int k) {   // a < b, not adjacent
-        const size_t ab = (size_t)a * n + b;
-        const int32_t L = h->sep_len[ab];
-        for (int t = 0; t < L; ++t)
-            if (h->sep_members[(size_t)h->sep_off[ab] + t] == k) return true;
+        const long long r = find_sepset(h, a, b);
+        if (r < 0) return false;
+        for (int64_t t = h->csr_offs[r]; t < h->csr_offs[r + 1]; ++t)
+            if (h->csr_members[(size_t)t] == k) return true;
         return false;
     };
     // step 2: arrowheads of the unshielded colliders
