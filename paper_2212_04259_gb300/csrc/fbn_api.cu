@@ -94,12 +94,9 @@ struct Workspace {
     long long* crit_keys = nullptr;
     double* crit_vals = nullptr;
     double crit_alpha = -1.0;
-    cudaEvent_t ev[FBN_MAX_DEPTHS + 1] = {};
-    cudaEvent_t kev[2 * FBN_MAX_DEPTHS + 2] = {};   // test kernels of each depth; the Gram
-    cudaEvent_t done[FBN_MAX_DEPTHS] = {};          // loop flag of each depth copied to the host
+    cudaEvent_t kev[2 * FBN_MAX_DEPTHS + 2] = {};   // the Gram's window at the end
     DepthRecord* d_rec = nullptr;
     DepthRecord* h_rec = nullptr;                   // pinned
-    int* h_active = nullptr;                        // pinned, one flag per depth
     long long gs_cells = 0;                         // cells per group of the global scratch
     // one-hot Gram of a whole batch
     uint8_t* gram_E = nullptr;                      // one-hot matrices, problem after problem
@@ -130,11 +127,10 @@ struct Workspace {
     // one-hot layout of the last prepare_gram and the last one whose pad rows
     // were zeroed (k_onehot writes only the rows below M)
     std::vector<long long> gram_layout, gram_zeroed;
-    // CUDA graphs of one generic depth: [parity][big-table class queued]
-    cudaGraphExec_t graph[2][2] = {};
+    // the graph of the generic depths (a device-driven while loop)
+    cudaGraphExec_t loop = nullptr;
     std::vector<uint8_t> graph_key;
-    cudaEvent_t gkev[2][2] = {};   // test-kernel window per parity
-    cudaEvent_t gdone[2] = {};     // loop flag copied, per parity
+    cudaEvent_t tev[2][2] = {};   // test-kernel windows of depths 0 and 1 when launched directly
     bool events = false;
 
     void release()
@@ -148,21 +144,13 @@ struct Workspace {
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
         dfree(split_tab); dfree(split_ticket);
         if (events) {
-            for (auto& e : ev) cudaEventDestroy(e);
             for (auto& e : kev) cudaEventDestroy(e);
-            for (auto& e : done) cudaEventDestroy(e);
-        }
-        for (auto& row : graph)
-            for (auto& g : row)
-                if (g) cudaGraphExecDestroy(g);
-        if (events) {
-            for (auto& row : gkev)
+            for (auto& row : tev)
                 for (auto& e : row) cudaEventDestroy(e);
-            for (auto& e : gdone) cudaEventDestroy(e);
         }
+        if (loop) cudaGraphExecDestroy(loop);
         dfree(d_rec);
         if (h_rec) cudaFreeHost(h_rec);
-        if (h_active) cudaFreeHost(h_active);
         if (h_up) cudaFreeHost(h_up);
         h_maps.clear();
         gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr; pk = nullptr;
@@ -268,16 +256,12 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
     if (!ws.d_ctr) {
         CK(dalloc(&ws.d_ctr, 1));
         CK(cudaMallocHost((void**)&ws.h_ctr, sizeof(DepthCounters)));
-        for (auto& e : ws.ev) CK(cudaEventCreate(&e));
         for (auto& e : ws.kev) CK(cudaEventCreate(&e));
-        for (auto& e : ws.done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        for (auto& row : ws.gkev)
+        for (auto& row : ws.tev)
             for (auto& e : row) CK(cudaEventCreate(&e));
-        for (auto& e : ws.gdone) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         ws.events = true;
         CK(dalloc(&ws.d_rec, kMaxDepthRecords));
         CK(cudaMallocHost((void**)&ws.h_rec, kMaxDepthRecords * sizeof(DepthRecord)));
-        CK(cudaMallocHost((void**)&ws.h_active, kMaxDepthRecords * sizeof(int)));
         const int orc = ensure_order(h, ws, kMaxPasses);
         if (orc) return orc;
         CK(dalloc(&ws.crit_keys, kCritCap));
@@ -703,8 +687,6 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
                                      (long long)grid_big};
     double mean_n = 0;
     for (int p = 0; p < k; ++p) mean_n += (double)hs[p]->N / k;
-    int max_ar = 2;
-    for (int p = 0; p < k; ++p) max_ar = std::max(max_ar, hs[p]->max_arity);
     const int grid_aux = dev_sms * 4;   // grid-stride helpers (ordering, removal)
     // ranks per chunk: fixed by the option, else chosen on the device per depth
     const int gs_forced = plain ? 1 : h->opt.group_size;
@@ -722,6 +704,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     CK(cudaMemsetAsync(ws.cursor, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
     DepthCounters c0{};
     c0.active = 1;
+    c0.rec = ws.d_rec;
     *ws.h_ctr = c0;
     CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
 
@@ -747,10 +730,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     }
     ws.split_dirty = true;   // until this call completes its loop
 
-    // The kernels of one depth after the edge list: ordering + pool per class,
-    // then removal and the end of the depth.
-    auto enqueue_tests = [&](bool big_possible) -> int {
-        const int nclass = big_possible ? 2 : 1;
+    // The kernels of one depth after the edge list: ordering and the pool of
+    // each class; then removal and the end of the depth.
+    auto enqueue_tests = [&]() {
+        const int nclass = 2;
         if (!plain) {   // both classes ordered up front: their sorted orders do not overlap
             ScanClass sc[2];
             for (int cls = 0; cls < 2; ++cls) {
@@ -781,33 +764,82 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             a.sorted = ws.sorted;
             launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
         }
-        return plain ? nclass : 2 + nclass;
     };
     auto enqueue_head = [&]() {
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
         launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, gs_forced, gs_edges, ws.binom, ws.brows, wcap,
                      ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
     };
-    // events inside a captured graph must be recorded as external event nodes
-    auto record = [&](cudaEvent_t ev, bool capturing) {
-        return capturing ? cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal) : cudaEventRecord(ev, st);
-    };
-    auto enqueue_tail = [&](int* active_dst, cudaEvent_t done_ev, bool capturing) -> int {
+    auto enqueue_tail = [&]() {
         launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
                      grid_aux, st);
         launch_depth_end(ws.d_ctr, ws.d_rec, max_depth, ws.hist, ws.cursor, st);
-        CK(cudaMemcpyAsync(active_dst, &ws.d_ctr->active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(record(done_ev, capturing));
-        return FBN_OK;
     };
-    auto big_at = [&](int d) {   // the big-table class is possible once max_arity^(d+2) tops the bound
-        long long bound = 1;
-        for (int q = 0; q < d + 2 && bound <= wcap; ++q) bound *= max_ar;
-        return bound > wcap;
+    const int body_launches = plain ? 7 : 9;
+    auto capture_loop = [&]() -> cudaError_t {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        if (e != cudaSuccess) return e;
+        auto give_up = [&](cudaError_t err) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t tmp = nullptr;
+                cudaStreamEndCapture(st, &tmp);
+            }
+            cudaGetLastError();
+            cudaGraphDestroy(g);
+            return err;
+        };
+        cudaGraphConditionalHandle cond{};
+        if ((e = cudaGraphConditionalHandleCreate(&cond, g, 0, 0)) != cudaSuccess) return give_up(e);
+        // top level: the first depth's edge list and the loop condition
+        if ((e = cudaStreamBeginCaptureToGraph(st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return give_up(e);
+        enqueue_head();
+        launch_gate(ws.d_ctr, cond, st);
+        cudaGraphNode_t gate_node = nullptr;
+        {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            const cudaGraphNode_t* deps = nullptr;
+            size_t nd = 0;
+            if ((e = cudaStreamGetCaptureInfo(st, &cs, nullptr, nullptr, &deps, nullptr, &nd)) != cudaSuccess)
+                return give_up(e);
+            if (cs != cudaStreamCaptureStatusActive || nd != 1) return give_up(cudaErrorStreamCaptureInvalidated);
+            gate_node = deps[0];
+        }
+        cudaGraph_t out = nullptr;
+        if ((e = cudaStreamEndCapture(st, &out)) != cudaSuccess) return give_up(e);
+        // the while node and its body: one depth, then the next one's edge list
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t cn = nullptr;
+        if ((e = cudaGraphAddNode(&cn, g, &gate_node, nullptr, 1, &cp)) != cudaSuccess) return give_up(e);
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        if ((e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+            cudaSuccess)
+            return give_up(e);
+        enqueue_tests();
+        enqueue_tail();
+        enqueue_head();
+        launch_gate(ws.d_ctr, cond, st);
+        if ((e = cudaStreamEndCapture(st, &out)) != cudaSuccess) return give_up(e);
+        e = cudaGraphInstantiate(&ws.loop, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ws.loop = nullptr;
+            cudaGetLastError();
+        }
+        return e;
     };
 
-    // Graphs of a generic depth, captured once per configuration: every
-    // argument they hold goes into the key.
+    // The generic depths as one graph: the edge list of the first one, then a
+    // device-driven while loop whose body tests a depth, removes its edges,
+    // ends it and lists the next depth's edges (k_gate: go on or stop).
+    // Captured once per configuration: every argument it holds is in the key.
     {
         std::vector<uint8_t> key;
         auto put = [&](const void* p, size_t n) {
@@ -816,87 +848,75 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         };
         const void* ptrs[] = {ws.probs, ws.vtx_prob, ws.vtx_first, ws.binom, ws.edges, ws.min_accept, ws.d_ctr,
                               ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.gscratch, ws.sep_pool, ws.d_rec,
-                              ws.h_active, ws.crit_keys, ws.crit_vals, ws.split_tab, ws.split_ticket, (void*)st};
+                              ws.crit_keys, ws.crit_vals, ws.split_tab, ws.split_ticket};
         put(ptrs, sizeof ptrs);
         const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
-                                  grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain, max_ar,
+                                  grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain,
                                   h->opt.statistic, h->opt.df_mode,
                                   groups[0], groups[1], groups[2], groups[3]};
         put(ints, sizeof ints);
         put(&mean_n, sizeof mean_n);
         put(&alpha, sizeof alpha);
         if (key != ws.graph_key) {
-            for (auto& row : ws.graph)
-                for (auto& g : row)
-                    if (g) {
-                        cudaGraphExecDestroy(g);
-                        g = nullptr;
-                    }
-            for (int par = 0; par < 2; ++par)
-                for (int big = 0; big < 2; ++big) {
-                    cudaGraph_t graph = nullptr;
-                    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-                    enqueue_head();
-                    record(ws.gkev[par][0], true);
-                    enqueue_tests(big != 0);
-                    record(ws.gkev[par][1], true);
-                    enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], true);
-                    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
-                    if (ce != cudaSuccess) return fail(h, FBN_ECUDA, "depth graph capture: %s", cudaGetErrorString(ce));
-                    const cudaError_t ie = cudaGraphInstantiate(&ws.graph[par][big], graph, 0);
-                    cudaGraphDestroy(graph);
-                    if (ie != cudaSuccess) return fail(h, FBN_ECUDA, "depth graph: %s", cudaGetErrorString(ie));
-                }
+            if (ws.loop) cudaGraphExecDestroy(ws.loop);
+            ws.loop = nullptr;
+            ws.graph_key.clear();
+            // with programmatic launches first, else without (bodies of
+            // conditional nodes may refuse programmatic edges)
+            cudaError_t err = cudaSuccess;
+            for (int pdl = 1; pdl >= 0 && !ws.loop; --pdl) {
+                set_pdl(pdl != 0);
+                err = capture_loop();
+            }
+            set_pdl(true);
+            if (!ws.loop) return fail(h, FBN_ECUDA, "depth loop graph: %s", cudaGetErrorString(err));
             ws.graph_key = key;
         }
     }
 
     fbn_stats stats{};
-    int queued = 0;
-    for (int d = 0; d < kMaxDepthRecords - 2; ++d) {
-        if (max_depth >= 0 && d > max_depth) break;
-        CK(cudaEventRecord(ws.ev[d], st));
-        const int par = d & 1;
-        if (d == 0 && gram) {
-            enqueue_head();
-            CK(cudaEventRecord(ws.gkev[par][0], st));
-            rc = run_gram(h, ws, k, total_vtx, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS],
-                          ws.kev[2 * FBN_MAX_DEPTHS + 1]);
-            if (rc) return rc;
-            CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr,
-                                   h->opt.statistic, h->opt.df_mode, grid_aux, st));
-            CK(cudaEventRecord(ws.gkev[par][1], st));
-            rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
-            if (rc) return rc;
-            launches += 8;
-        } else if (d == 1 && nbr1) {
-            enqueue_head();
-            CK(cudaEventRecord(ws.gkev[par][0], st));
-            CK(launch_nbr1(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.edges, ws.min_accept, ct, alpha, ws.d_ctr,
-                           dev_sms, h->opt.wait_limit, st));
-            CK(cudaEventRecord(ws.gkev[par][1], st));
-            rc = enqueue_tail(&ws.h_active[kMaxDepthRecords - 2 + par], ws.gdone[par], false);
-            if (rc) return rc;
-            launches += 5;
-        } else {
-            const bool big = big_at(d);
-            CK(cudaGraphLaunch(ws.graph[par][big ? 1 : 0], st));
-            launches += 4 + (plain ? (big ? 2 : 1) : (big ? 4 : 3));
-        }
-        CK(cudaGetLastError());
-        queued = d + 1;
-        // depth d is queued; read depth d-1 (its slot is reused by depth d+1)
-        // and stop queueing once it ended the loop
-        if (d >= 1) {
-            const int pp = (d - 1) & 1;
-            CK(cudaEventSynchronize(ws.gdone[pp]));
-            float kms = 0.f;
-            CK(cudaEventElapsedTime(&kms, ws.gkev[pp][0], ws.gkev[pp][1]));
-            stats.test_ms[d - 1] = kms;
-            if (!ws.h_active[kMaxDepthRecords - 2 + pp]) break;
-        }
+    int d_loop = 0;   // first depth of the graph loop
+    bool direct[2] = {false, false};   // depths 0 and 1 launched directly (timed by events)
+    if (gram) {
+        enqueue_head();
+        CK(cudaEventRecord(ws.tev[0][0], st));
+        rc = run_gram(h, ws, k, total_vtx, &ws.d_ctr->status, ws.kev[2 * FBN_MAX_DEPTHS],
+                      ws.kev[2 * FBN_MAX_DEPTHS + 1]);
+        if (rc) return rc;
+        CK(launch_pairs_decide(ws.edges, ws.edge_cap, ws.probs, ws.min_accept, ct, alpha, ws.d_ctr,
+                               h->opt.statistic, h->opt.df_mode, grid_aux, st));
+        CK(cudaEventRecord(ws.tev[0][1], st));
+        enqueue_tail();
+        launches += 6;
+        direct[0] = true;
+        d_loop = 1;
     }
-    CK(cudaEventRecord(ws.ev[queued], st));
+    if (nbr1 && (max_depth < 0 || max_depth >= 1)) {
+        if (d_loop == 0) {   // depth 0 on the pool, launched directly
+            enqueue_head();
+            CK(cudaEventRecord(ws.tev[0][0], st));
+            enqueue_tests();
+            CK(cudaEventRecord(ws.tev[0][1], st));
+            enqueue_tail();
+            launches += body_launches - 1;
+            direct[0] = true;
+        }
+        enqueue_head();
+        CK(cudaEventRecord(ws.tev[1][0], st));
+        CK(launch_nbr1(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.edges, ws.min_accept, ct, alpha, ws.d_ctr,
+                       dev_sms, h->opt.wait_limit, st));
+        CK(cudaEventRecord(ws.tev[1][1], st));
+        enqueue_tail();
+        launches += 5;
+        direct[1] = true;
+        d_loop = 2;
+    }
+    const bool loop = max_depth < 0 || d_loop <= max_depth;
+    if (loop) {
+        CK(cudaGraphLaunch(ws.loop, st));
+        launches += 3;
+    }
+    CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(ws.h_rec, ws.d_rec, kMaxDepthRecords * sizeof(DepthRecord), cudaMemcpyDeviceToHost, st));
     if (adj_out)   // the adjacency goes out with the counters (dropped if the call is retried)
@@ -904,11 +924,13 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             if (adj_out[p])
                 CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, (size_t)hs[p]->n * hs[p]->n, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
-    if (queued > 0) {
-        float kms = 0.f;
-        CK(cudaEventElapsedTime(&kms, ws.gkev[(queued - 1) & 1][0], ws.gkev[(queued - 1) & 1][1]));
-        stats.test_ms[queued - 1] = kms;
-    }
+    if (loop) launches += (long long)body_launches * std::max(0, ws.h_ctr->d - d_loop);
+    for (int q = 0; q < 2; ++q)
+        if (direct[q]) {
+            float kms = 0.f;
+            CK(cudaEventElapsedTime(&kms, ws.tev[q][0], ws.tev[q][1]));
+            stats.test_ms[q] = kms;
+        }
     const DepthCounters& c = *ws.h_ctr;
     if (c.status == 0) ws.split_dirty = false;   // every split test's last part zeroed its table
     if (c.status & (kStatusSepPool | kStatusScratch)) {
@@ -928,22 +950,22 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     rc = check_status(h, c.status);
     if (rc) return rc;
 
-    for (int d = 0; d < queued; ++d) {
+    for (int d = 0; d < kMaxDepthRecords; ++d) {
         const DepthRecord& r = ws.h_rec[d];
-        if (r.edges == 0) {   // the depth that found no edge: Algorithm 1 stopped before it
-            stats.test_ms[d] = 0;
-            break;
-        }
+        if (r.edges == 0) break;   // the depth that found no edge: Algorithm 1 stopped before it
+        if (d >= FBN_MAX_DEPTHS) break;
         stats.depths = d + 1;
         stats.edges[d] = r.edges;
         stats.tests[d] = r.tests;
         stats.tests_oracle[d] = r.tests_oracle;
         stats.removed[d] = r.removed;
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, ws.ev[d], ws.ev[d + 1]));
-        stats.ms[d] = ms;
+        const unsigned long long next = d + 1 < kMaxDepthRecords ? ws.h_rec[d + 1].t_begin : 0;
+        const unsigned long long end = next > r.t_begin ? next : r.t_end;
+        stats.ms[d] = end > r.t_begin && r.t_begin ? (float)((end - r.t_begin) * 1e-6) : 0.f;
+        if (d >= d_loop && r.t_tests_end > r.t_tests && r.t_tests)
+            stats.test_ms[d] = (float)((r.t_tests_end - r.t_tests) * 1e-6);
     }
-    if (gram && queued > 0) {
+    if (gram) {
         float gms = 0.f;
         CK(cudaEventElapsedTime(&gms, ws.kev[2 * FBN_MAX_DEPTHS], ws.kev[2 * FBN_MAX_DEPTHS + 1]));
         stats.gram_ms = gms;

@@ -68,6 +68,15 @@ constexpr int kClassCta = 1;
 
 // Device-side state of the depth loop.  Per-depth fields are cleared by
 // k_depth_begin; d, active, status and sep_used persist across depths.
+// Per-depth record written by k_depth_end.
+constexpr int kMaxDepthRecords = 64;
+struct DepthRecord {
+    long long edges, tests, tests_oracle, removed;
+    // device clock (ns): depth start (snapshot), test kernels start and end,
+    // depth end; 0 where a kernel of the depth did not run
+    unsigned long long t_begin, t_tests, t_tests_end, t_end;
+};
+
 struct DepthCounters {
     unsigned long long n_edges[2];      // edges per class
     unsigned long long maxc[2];         // largest chunk count per class
@@ -88,6 +97,7 @@ struct DepthCounters {
     unsigned long long nbr_claim;       // vertex claims of the depth-1 tensor-core kernel
     unsigned long long max_total[2];    // largest rank count of an edge per class
     int split[2];                       // sample parts per test per class (1 = whole tests)
+    DepthRecord* rec;                   // per-depth records (persists)
 };
 
 // Tests split by samples: when a depth has few tests against the groups, every
@@ -97,12 +107,6 @@ struct DepthCounters {
 constexpr int kMaxSplit = 16;
 constexpr long long kSplitMinSamples = 4096;   // samples per part at least
 constexpr long long kSplitItems = 4096;        // tests split at once at most
-
-// Per-depth record written by k_depth_end.
-constexpr int kMaxDepthRecords = 64;
-struct DepthRecord {
-    long long edges, tests, tests_oracle, removed;
-};
 
 // Passes of the work pool are capped: an edge with more ranks than
 // kMaxPasses * gs takes chunks of ceil(total / kMaxPasses) ranks.

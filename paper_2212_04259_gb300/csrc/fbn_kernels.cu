@@ -42,6 +42,23 @@ __device__ __forceinline__ void pdl_enter()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Launches of the depth kernels go through launch_pdl; set_pdl(false)
+// launches them without the attribute.
+static bool g_pdl = true;
+
+// Device clock in nanoseconds, for the per-depth records.
+__device__ __forceinline__ unsigned long long gtime()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ DepthRecord* depth_rec(const DepthCounters* ctr, int d)
+{
+    return ctr->rec && d < kMaxDepthRecords ? ctr->rec + d : nullptr;
+}
+
 // --------------------------------------------------------------------------
 __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
                            const int32_t* __restrict__ vtx_first, int total_vertices, DepthCounters* ctr)
@@ -50,6 +67,8 @@ __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* 
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (g >= total_vertices || !ctr->active) return;
+    if (g == 0 && lane == 0)
+        if (DepthRecord* r = depth_rec(ctr, ctr->d)) r->t_begin = gtime();
     const int p = vtx_prob[g];
     const ProblemDev P = probs[p];
     const int v = g - vtx_first[p];
@@ -232,6 +251,8 @@ __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double me
     pdl_enter();
     __shared__ unsigned long long sh[32];
     if (!ctr->active) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        if (DepthRecord* r = depth_rec(ctr, ctr->d)) r->t_tests = gtime();
     const int cls = blockIdx.x;   // one CTA per edge class
     const ScanClass& sc = cls == 0 ? c0 : c1;
     const unsigned long long* __restrict__ hist = sc.hist;
@@ -576,6 +597,14 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     if (r == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
 }
 
+// The end of a test CTA in the depth's record (the latest over CTAs).
+__device__ __forceinline__ void tests_done(const DepthCounters* ctr)
+{
+    __syncthreads();
+    if (threadIdx.x == 0)
+        if (DepthRecord* r = depth_rec(ctr, ctr->d)) atomicMax(&r->t_tests_end, gtime());
+}
+
 // Small-table class: the group size k_scan chose for this depth.
 __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
 {
@@ -589,6 +618,7 @@ __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
         case 128: pool_body<128>(a, smem, sh); break;
         default: pool_body<kTestThreads>(a, smem, sh); break;
     }
+    tests_done(a.ctr);
 }
 
 // Big-table class: CTA groups.
@@ -599,6 +629,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_pool_big(PoolArgs a)
     __shared__ PoolShared sh;
     if (!a.ctr->active) return;
     pool_body<kTestThreads>(a, smem, sh);
+    tests_done(a.ctr);
 }
 
 __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
@@ -611,6 +642,8 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
     const DepthCounters* ctr = a.ctr;
     if (!ctr->active) return;
     const int d = ctr->d;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.cls == 0)
+        if (DepthRecord* r = depth_rec(ctr, d)) r->t_tests = gtime();
     const long long E = (long long)ctr->n_edges[a.cls];
     const long long cb = class_base(ctr, a.cls, a.edge_cap);
     int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
@@ -626,6 +659,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
         __syncthreads();
     }
     if (threadIdx.x == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
+    tests_done(ctr);
 }
 
 // --------------------------------------------------------------------------
@@ -703,6 +737,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
             rec[d].tests = (long long)ctr->tests;
             rec[d].tests_oracle = (long long)ctr->tests_oracle;
             rec[d].removed = (long long)ctr->removed;
+            rec[d].t_end = gtime();
         }
         const int next = d + 1;
         const bool stop = E == 0 || ctr->status != 0 || (max_depth >= 0 && next > max_depth) || next > kMaxD ||
@@ -728,6 +763,17 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
             cc[k] = 0;
         }
     }
+}
+
+// Condition of the depth loop's graph (one thread), after the edge list of
+// the next depth: go on while Algorithm 1 continues and the depth has an edge
+// to test (no edge with a side of at least d candidates: the loop ends).
+__global__ void k_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop)
+{
+    pdl_enter();
+    const bool go = ctr->active && ctr->n_edges[0] + ctr->n_edges[1] > 0;
+    if (!go) ctr->active = 0;
+    cudaGraphSetConditional(loop, go ? 1u : 0u);
 }
 
 // --------------------------------------------------------------------------
@@ -803,7 +849,7 @@ static void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = g_pdl ? 1 : 0;
     cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
@@ -860,6 +906,16 @@ void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsig
                       unsigned long long* cursor, cudaStream_t st)
 {
     launch_pdl(k_depth_end, dim3(1), dim3(256), 0, st, ctr, rec, max_depth, hist, cursor);
+}
+
+void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream_t st)
+{
+    launch_pdl(k_gate, dim3(1), dim3(1), 0, st, ctr, loop);
+}
+
+void set_pdl(bool on)
+{
+    g_pdl = on;
 }
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,

@@ -34,6 +34,10 @@ void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned
                   DepthCounters* ctr, int grid, cudaStream_t st);
 void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
                       unsigned long long* cursor, cudaStream_t st);
+// The depth loop's condition: 1 while the next depth has an edge to test.
+void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream_t st);
+// Programmatic dependent launch for the depth kernels (on by default).
+void set_pdl(bool on);
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
                      size_t smem_bytes, int stat, int df_mode, cudaStream_t st);
