@@ -28,6 +28,7 @@ constexpr size_t kSmemBytes = 100 * 1024;     // dynamic shared memory of a CTA 
 constexpr long long kSplitStride = 4096;        // cells of a split test's global table at most
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
+constexpr int kCritDense = 8192;              // critical values kept densely: df < kCritDense
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
@@ -93,6 +94,7 @@ struct Workspace {
     long long gscratch_total = 0;
     long long* crit_keys = nullptr;
     double* crit_vals = nullptr;
+    double* crit_dense = nullptr;
     double crit_alpha = -1.0;
     cudaEvent_t kev[2 * FBN_MAX_DEPTHS + 2] = {};   // the Gram's window at the end
     DepthRecord* d_rec = nullptr;
@@ -140,7 +142,7 @@ struct Workspace {
         dfree(d_ctr);
         if (h_ctr) cudaFreeHost(h_ctr);
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
-        dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals);
+        dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals); dfree(crit_dense);
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
         dfree(split_tab); dfree(split_ticket);
         if (events) {
@@ -266,6 +268,7 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         if (orc) return orc;
         CK(dalloc(&ws.crit_keys, kCritCap));
         CK(dalloc(&ws.crit_vals, kCritCap));
+        CK(dalloc(&ws.crit_dense, kCritDense));
         CK(dalloc(&ws.split_tab, kSplitItems * kSplitStride));
         CK(dalloc(&ws.split_ticket, kSplitItems));
         ws.split_dirty = true;
@@ -693,11 +696,9 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     const long long gs_edges = 8LL * grid_small * 8;   // live edges from which 4 ranks per claim pay
     const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
     const int forced = h->opt.group_threads;
-    if (ws.crit_alpha != alpha) {
-        CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
-        ws.crit_alpha = alpha;
-    }
-    CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, 0};
+    const bool new_alpha = ws.crit_alpha != alpha;
+    if (new_alpha) CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
+    CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, kCritDense, ws.crit_dense};
 
     CK(cudaMemsetAsync(ws.d_rec, 0, kMaxDepthRecords * sizeof(DepthRecord), st));
     CK(cudaMemsetAsync(ws.hist, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
@@ -707,6 +708,11 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     c0.rec = ws.d_rec;
     *ws.h_ctr = c0;
     CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
+    if (new_alpha) {   // after the counters: an iteration cap sets their status
+        launch_crit_fill(alpha, ws.crit_dense, kCritDense, &ws.d_ctr->status, st);
+        CK(cudaGetLastError());
+        launches += 1;
+    }
 
     PoolArgs base{};
     base.probs = ws.probs;
@@ -848,7 +854,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         };
         const void* ptrs[] = {ws.probs, ws.vtx_prob, ws.vtx_first, ws.binom, ws.edges, ws.min_accept, ws.d_ctr,
                               ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.gscratch, ws.sep_pool, ws.d_rec,
-                              ws.crit_keys, ws.crit_vals, ws.split_tab, ws.split_ticket};
+                              ws.crit_keys, ws.crit_vals, ws.crit_dense, ws.split_tab, ws.split_ticket};
         put(ptrs, sizeof ptrs);
         const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
                                   grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain,
@@ -949,6 +955,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     }
     rc = check_status(h, c.status);
     if (rc) return rc;
+    ws.crit_alpha = alpha;   // the dense critical values are complete for this alpha
 
     for (int d = 0; d < kMaxDepthRecords; ++d) {
         const DepthRecord& r = ws.h_rec[d];

@@ -90,10 +90,11 @@ __device__ __forceinline__ double chisq_crit(double df, double alpha, unsigned* 
     return x;
 }
 
-// Open-addressing cache of critical values keyed by df (for one alpha).  A
-// slot is claimed with a CAS to -1, filled, then published with a release
-// store of the key; readers that see -1 compute the value themselves, so no
-// thread ever waits on another.
+// Critical values for one alpha: a dense table for small df (filled by a
+// kernel before the depth loop, read-only while it runs), then an
+// open-addressing cache keyed by df.  A cache slot is claimed with a CAS to
+// -1, filled, then published with a release store of the key; readers that
+// see -1 compute the value themselves, so no thread ever waits on another.
 using CritTable = CritTableDev;
 
 __device__ __forceinline__ long long ld_acquire(const long long* p)
@@ -110,6 +111,7 @@ __device__ __forceinline__ void st_release(long long* p, long long v)
 
 __device__ __forceinline__ double crit_get(const CritTable& t, long long df, double alpha, unsigned* status)
 {
+    if (df < t.dense_n) return __ldg(t.dense + df);
     unsigned h = (unsigned)(df * 0x9E3779B97F4A7C15ULL >> 40) & (unsigned)(t.cap - 1);
     for (int probe = 0; probe < 32; ++probe, h = (h + 1) & (unsigned)(t.cap - 1)) {
         const long long k = ld_acquire(t.keys + h);
@@ -507,9 +509,12 @@ __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 template <int G>
 __device__ __forceinline__ int pick_mode(long long C, long long marg, long long slice_ints, int N)
 {
-    if (C * G + C + marg <= slice_ints) return kLane;
+    // private copies cost their zeroing and folding (C words per copy); they
+    // pay only while that stays below the samples counted (short sample
+    // ranges: split tests, small problems, take fewer copies)
+    if (C * G + C + marg <= slice_ints && C * G <= N) return kLane;
     if (G == 32 && N >= 65536 && N / 32 + 32 < 65536 && (C + 1) / 2 * 32 + C + marg <= slice_ints) return kLane16;
-    if (Grp<G>::kWarps > 1 && C * Grp<G>::kWarps + marg <= slice_ints) return kWarp;
+    if (Grp<G>::kWarps > 1 && C * Grp<G>::kWarps + marg <= slice_ints && 2 * C * Grp<G>::kWarps <= N) return kWarp;
     if (C + marg <= slice_ints) return kShared;
     return kGlobal;
 }
@@ -532,7 +537,7 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
     constexpr int W = Grp<G>::kWarps;
     int* cnt = mode == kGlobal ? gtab : slice;
     const long long zero_n = mode == kLane ? C * G : mode == kLane16 ? (C + 1) / 2 * 32 : mode == kWarp ? C * W : C;
-    for (long long k = r; k < zero_n; k += G) cnt[k] = 0;
+    for (int k = r; k < (int)zero_n; k += G) cnt[k] = 0;   // zero_n <= 2^27
     Grp<G>::sync();
     switch (mode) {
         case kLane: count_dispatch<G, kLane>(s, cnt + (long long)warp * C * 32 + lane); break;
@@ -544,7 +549,7 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
     int* T;
     if (mode == kLane16) {   // one warp: lane l folds the 32 columns of cells l, l + 32, ...
         T = slice + (C + 1) / 2 * 32;
-        for (long long c = lane; c < C; c += 32) {
+        for (int c = lane; c < (int)C; c += 32) {
             const int* row = cnt + (c >> 1) * 32;
             const int sh = (int)(c & 1) * 16;
             int sum = 0;
@@ -559,7 +564,7 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
         // row, which only that lane touches (and which keeps stage 2 free of
         // bank conflicts).  stage 2: fold the warps' partial sums.
         int* own = cnt + (long long)warp * C * 32;
-        for (long long c = lane; c < C; c += 32) {
+        for (int c = lane; c < (int)C; c += 32) {
             const int* col = own + c * 32;
             int sum = 0;
 #pragma unroll 8
@@ -568,17 +573,17 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
         }
         Grp<G>::sync();
         T = slice + C * G;
-        for (long long c = r; c < C; c += G) {
+        for (int c = r; c < (int)C; c += G) {
             int sum = 0;
-            for (int w = 0; w < W; ++w) sum += cnt[((long long)w * C + c) * 32 + (c & 31)];
+            for (int w = 0; w < W; ++w) sum += cnt[(w * (int)C + c) * 32 + (c & 31)];
             T[c] = sum;
         }
         *M = T + C;
     } else if (mode == kWarp) {
         T = cnt;
-        for (long long c = r; c < C; c += G) {
+        for (int c = r; c < (int)C; c += G) {
             int sum = 0;
-            for (int w = 0; w < W; ++w) sum += cnt[(long long)w * C + c];
+            for (int w = 0; w < W; ++w) sum += cnt[w * (int)C + c];
             T[c] = sum;
         }
         *M = slice + C * W;
@@ -597,27 +602,29 @@ __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, i
 template <int G>
 __device__ __forceinline__ void grp_marginals(const TestSpec& s, const int* T, int* M)
 {
-    const long long nz = s.cells / (s.rx * s.ry);
+    // cells <= kMaxCells < 2^31: 32-bit indices throughout
+    const int rx = s.rx, ry = s.ry;
+    const int nz = (int)s.cells / (rx * ry);
     int* Nxz = M;
-    int* Nyz = M + nz * s.rx;
-    int* Nzz = Nyz + nz * s.ry;
+    int* Nyz = M + nz * rx;
+    int* Nzz = Nyz + nz * ry;
     const int r = Grp<G>::rank();
-    for (long long k = r; k < nz * s.rx; k += G) {
+    for (int k = r; k < nz * rx; k += G) {
         int sum = 0;
-        for (int y = 0; y < s.ry; ++y) sum += T[k * s.ry + y];
+        for (int y = 0; y < ry; ++y) sum += T[k * ry + y];
         Nxz[k] = sum;
     }
-    for (long long k = r; k < nz * s.ry; k += G) {
-        const long long z = k / s.ry;
-        const int y = (int)(k - z * s.ry);
+    for (int k = r; k < nz * ry; k += G) {
+        const int z = k / ry;
+        const int y = k - z * ry;
         int sum = 0;
-        for (int x = 0; x < s.rx; ++x) sum += T[(z * s.rx + x) * s.ry + y];
+        for (int x = 0; x < rx; ++x) sum += T[(z * rx + x) * ry + y];
         Nyz[k] = sum;
     }
     Grp<G>::sync();
-    for (long long z = r; z < nz; z += G) {
+    for (int z = r; z < nz; z += G) {
         int sum = 0;
-        for (int x = 0; x < s.rx; ++x) sum += Nxz[z * s.rx + x];
+        for (int x = 0; x < rx; ++x) sum += Nxz[z * rx + x];
         Nzz[z] = sum;
     }
     Grp<G>::sync();
@@ -631,21 +638,21 @@ template <int G>
 __device__ __forceinline__ double grp_g2_exact(const TestSpec& s, const int* T, const int* M, double* red,
                                                int32_t* table_out)
 {
-    const long long nz = s.cells / (s.rx * s.ry);
-    const int rxy = s.rx * s.ry;
+    const int rx = s.rx, ry = s.ry, rxy = rx * ry, C = (int)s.cells;
+    const int nz = C / rxy;
     const int* Nxz = M;
-    const int* Nyz = M + nz * s.rx;
-    const int* Nzz = Nyz + nz * s.ry;
+    const int* Nyz = M + nz * rx;
+    const int* Nzz = Nyz + nz * ry;
     double acc = 0.0;
-    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+    for (int c = Grp<G>::rank(); c < C; c += G) {
         const int n = T[c];
         if (table_out) table_out[c] = n;
         if (n == 0) continue;
-        const long long z = c / rxy;
-        const int rem = (int)(c - z * rxy);
-        const int x = rem / s.ry, y = rem - x * s.ry;
+        const int z = c / rxy;
+        const int rem = c - z * rxy;
+        const int x = rem / ry, y = rem - x * ry;
         const long long a = (long long)n * Nzz[z];
-        const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
+        const long long b = (long long)Nxz[z * rx + x] * Nyz[z * ry + y];
         acc += (double)n * log1p((double)(a - b) / (double)b);
     }
     return 2.0 * grp_sum<G>(acc, red);
@@ -662,19 +669,19 @@ template <int G>
 __device__ __forceinline__ double grp_x2_exact(const TestSpec& s, const int* T, const int* M, double* red,
                                                int32_t* table_out)
 {
-    const long long nz = s.cells / (s.rx * s.ry);
-    const int rxy = s.rx * s.ry;
+    const int rx = s.rx, ry = s.ry, rxy = rx * ry, C = (int)s.cells;
+    const int nz = C / rxy;
     const int* Nxz = M;
-    const int* Nyz = M + nz * s.rx;
-    const int* Nzz = Nyz + nz * s.ry;
+    const int* Nyz = M + nz * rx;
+    const int* Nzz = Nyz + nz * ry;
     double acc = 0.0;
-    for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+    for (int c = Grp<G>::rank(); c < C; c += G) {
         const int n = T[c];
         if (table_out) table_out[c] = n;
-        const long long z = c / rxy;
-        const int rem = (int)(c - z * rxy);
-        const int x = rem / s.ry, y = rem - x * s.ry;
-        const long long nx = Nxz[z * s.rx + x], ny = Nyz[z * s.ry + y];
+        const int z = c / rxy;
+        const int rem = c - z * rxy;
+        const int x = rem / ry, y = rem - x * ry;
+        const long long nx = Nxz[z * rx + x], ny = Nyz[z * ry + y];
         if (nx == 0 || ny == 0) continue;
         const double dd = (double)((long long)n * Nzz[z] - nx * ny);
         acc += dd * dd / ((double)Nzz[z] * (double)nx * (double)ny);
@@ -687,14 +694,15 @@ __device__ __forceinline__ double grp_x2_exact(const TestSpec& s, const int* T, 
 template <int G>
 __device__ __forceinline__ long long grp_df_adjusted(const TestSpec& s, const int* M, double* red)
 {
-    const long long nz = s.cells / (s.rx * s.ry);
+    const int rx = s.rx, ry = s.ry;
+    const int nz = (int)s.cells / (rx * ry);
     const int* Nxz = M;
-    const int* Nyz = M + nz * s.rx;
+    const int* Nyz = M + nz * rx;
     double acc = 0.0;
-    for (long long z = Grp<G>::rank(); z < nz; z += G) {
+    for (int z = Grp<G>::rank(); z < nz; z += G) {
         int ax = 0, ay = 0;
-        for (int x = 0; x < s.rx; ++x) ax += Nxz[z * s.rx + x] > 0;
-        for (int y = 0; y < s.ry; ++y) ay += Nyz[z * s.ry + y] > 0;
+        for (int x = 0; x < rx; ++x) ax += Nxz[z * rx + x] > 0;
+        for (int y = 0; y < ry; ++y) ay += Nyz[z * ry + y] > 0;
         if (ax > 0 && ay > 0) acc += (double)(ax - 1) * (double)(ay - 1);
     }
     return (long long)(grp_sum<G>(acc, red) + 0.5);
@@ -718,18 +726,18 @@ template <int G>
 __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, const int* M, double crit,
                                            double* red, int stat = kStatG2)
 {
-    const long long nz = s.cells / (s.rx * s.ry);
-    const int rxy = s.rx * s.ry;
+    const int rx = s.rx, ry = s.ry, rxy = rx * ry, C = (int)s.cells;
+    const int nz = C / rxy;
     const int* Nxz = M;
-    const int* Nyz = M + nz * s.rx;
-    const int* Nzz = Nyz + nz * s.ry;
+    const int* Nyz = M + nz * rx;
+    const int* Nzz = Nyz + nz * ry;
     float acc = 0.0f, mag = 0.0f;
     if (stat == kStatX2) {
-        for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
-            const long long z = c / rxy;
-            const int rem = (int)(c - z * rxy);
-            const int x = rem / s.ry, y = rem - x * s.ry;
-            const int nx = Nxz[z * s.rx + x], ny = Nyz[z * s.ry + y];
+        for (int c = Grp<G>::rank(); c < C; c += G) {
+            const int z = c / rxy;
+            const int rem = c - z * rxy;
+            const int x = rem / ry, y = rem - x * ry;
+            const int nx = Nxz[z * rx + x], ny = Nyz[z * ry + y];
             if (nx == 0 || ny == 0) continue;
             const float fd = (float)((long long)T[c] * Nzz[z] - (long long)nx * ny);
             const float t = fd * fd / ((float)Nzz[z] * (float)nx * (float)ny);
@@ -737,14 +745,14 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
         }
         mag = acc;
     } else {
-        for (long long c = Grp<G>::rank(); c < s.cells; c += G) {
+        for (int c = Grp<G>::rank(); c < C; c += G) {
             const int n = T[c];
             if (n == 0) continue;
-            const long long z = c / rxy;
-            const int rem = (int)(c - z * rxy);
-            const int x = rem / s.ry, y = rem - x * s.ry;
+            const int z = c / rxy;
+            const int rem = c - z * rxy;
+            const int x = rem / ry, y = rem - x * ry;
             const long long a = (long long)n * Nzz[z];
-            const long long b = (long long)Nxz[z * s.rx + x] * Nyz[z * s.ry + y];
+            const long long b = (long long)Nxz[z * rx + x] * Nyz[z * ry + y];
             const float fb = (float)b;
             const float delta = (float)(a - b) / fb;
             const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);

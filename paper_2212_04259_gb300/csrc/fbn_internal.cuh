@@ -138,7 +138,8 @@ struct CritTableDev {
     long long* keys;
     double* vals;
     int cap;
-    int pad;
+    int dense_n;           // df < dense_n: dense[df], filled before the depth loop
+    const double* dense;
 };
 
 // Work pool of one depth and one edge class.  Sizes, the depth and the class

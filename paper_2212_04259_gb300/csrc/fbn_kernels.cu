@@ -467,7 +467,9 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
     int* Tg = a.split_tab + (long long)S.item * a.split_stride;
     if (r == 0) S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
     Grp<G>::sync();
+    bool ready = false;   // spec holds this rank's table shape (uniform over the group)
     if (S.go && setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) {
+        ready = true;
         const long long N = P.N;
         const long long lo = (N * S.part / split) & ~15LL;
         const long long hi = S.part == split - 1 ? N : ((N * (S.part + 1) / split) & ~15LL);
@@ -492,9 +494,11 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
     if (r == 0) S.ticket = atomicAdd(&a.split_ticket[S.item], 1u);
     Grp<G>::sync();
     if (S.ticket != (unsigned)(split - 1)) return 0;
-    // the last part: every other part's adds are in L2
+    // the last part: every other part's adds are in L2; the decision needs
+    // the table's shape only (cells, radices), which this part's own setup
+    // left in spec when it counted
     __threadfence();
-    if (!setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
+    if (!ready && !setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
     const long long C = spec.cells;
     int* Tl = slice;
     for (long long c = r; c < C; c += G) {
@@ -776,6 +780,14 @@ __global__ void k_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop)
     cudaGraphSetConditional(loop, go ? 1u : 0u);
 }
 
+// Dense critical values crit[df] for 1 <= df < n (crit[0] unused).
+__global__ void k_crit_fill(double alpha, double* __restrict__ dense, int n, unsigned* status)
+{
+    const int df = blockIdx.x * blockDim.x + threadIdx.x;
+    if (df >= n) return;
+    dense[df] = df == 0 ? 0.0 : chisq_crit((double)df, alpha, status);
+}
+
 // --------------------------------------------------------------------------
 // Explicit tests (fbn_ci_test / fbn_ci_table): exact FP64 G^2 and p-value.
 __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __restrict__ prob,
@@ -916,6 +928,11 @@ void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream
 void set_pdl(bool on)
 {
     g_pdl = on;
+}
+
+void launch_crit_fill(double alpha, double* dense, int n, unsigned* status, cudaStream_t st)
+{
+    k_crit_fill<<<(n + 127) / 128, 128, 0, st>>>(alpha, dense, n, status);
 }
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
