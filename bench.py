@@ -486,14 +486,17 @@ def main():
             F.fbn_learn_skeleton(hs_e2e[0], w["alpha"], w["max_depth"], adj_out=adjs_host[0])
         else:
             F.fbn_learn_skeleton_batch(hs_e2e, w["alpha"], w["max_depth"], adj_out=adjs_host)
-        members = 0
+        removed = members = 0
         for hh in hs_e2e:
-            _, _, mem = F.fbn_export_sepsets(hh, as_dict=False)
+            prs, _, mem = F.fbn_export_sepsets(hh, as_dict=False)
+            removed += len(prs)
             members += len(mem)
         torch.cuda.synchronize()
         if it > 0:   # the first pass warms the handle
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        d2h = sum(hh.n * hh.n * 13 for hh in hs_e2e) + 4 * members
+        # adjacency, the two CSR totals, pairs and offsets of the removed
+        # pairs, the members
+        d2h = sum(hh.n * hh.n + 16 for hh in hs_e2e) + 16 * removed + 4 * members
     e2e = {"value": world * tests / (statistics.median(e2e_ms) / 1e3), "unit": "tests/s",
            "h2d_bytes_per_step": int(sum(hh.numel() for hh in hosts)), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": statistics.median(e2e_ms)}
