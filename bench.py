@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--form", choices=["pool", "plain"], default="pool")
     ap.add_argument("--gs", type=int, default=0)
     ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
+    ap.add_argument("--loop", choices=["device", "host"], default="device",
+                    help="who drives the depth loop (host: the same kernels depth by depth, for kernel-by-kernel "
+                         "profilers)")
     ap.add_argument("--depth1", choices=["auto", "pool", "tensor"], default="auto",
                     help="depth-1 counting: tensor-core neighbourhood product or work pool")
     ap.add_argument("--statistic", choices=["g2", "x2"], default="g2", help="CI statistic (G^2 or Pearson X^2)")
@@ -97,7 +100,9 @@ def workload_config(name, w, args):
     cfg = {"workload": name, "form": args.form, "group_size": args.gs or "per depth (1 or 4)",
            "l2": "flushed by a 256 MB device write before each timed step"}
     if args.statistic != "g2" or args.df != "fixed":
-        cfg.update(statistic=args.statistic, df=args.df)
+        cfg.update(statistic=args.statistic, df=args.df, loop=args.loop)
+    if args.loop != "device":
+        cfg.update(loop=args.loop)
     if w["kind"] == "single":
         n, N = w["data"].shape
         cfg.update(n_vars=n, n_samples=N, alpha=w["alpha"], max_depth=w["max_depth"],
@@ -354,13 +359,13 @@ def main():
         data_dev = torch.from_numpy(w["data"]).cuda()
         handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local,
                                 group_threads=args.group_threads, depth1=args.depth1, statistic=args.statistic,
-                                df=args.df)]
+                                df=args.df, loop=args.loop)]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((w["data"].shape[0],) * 2, dtype=torch.uint8, device="cuda")]
     else:
         handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local,
                                 group_threads=args.group_threads, depth1=args.depth1, statistic=args.statistic,
-                                df=args.df)
+                                df=args.df, loop=args.loop)
                    for d, a in w["probs"]]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8, device="cuda") for d, _ in w["probs"]]
@@ -466,14 +471,14 @@ def main():
         n = w["data"].shape[0]
         adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
         he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local, depth1=args.depth1,
-                          statistic=args.statistic, df=args.df)
+                          statistic=args.statistic, df=args.df, loop=args.loop)
         F.fbn_set_stream(he, stream)
         hs_e2e, hosts, adjs_host = [he], [host], [adj_host]
     else:
         hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
         adjs_host = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8).pin_memory() for d, _ in w["probs"]]
         hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local, depth1=args.depth1,
-                               statistic=args.statistic, df=args.df)
+                               statistic=args.statistic, df=args.df, loop=args.loop)
                   for hh, (_, a) in zip(hosts, w["probs"])]
         F.fbn_set_stream(hs_e2e[0], stream)
     e2e_ms, d2h = [], 0

@@ -53,6 +53,11 @@ extern "C" {
 #define FBN_DF_ADJUSTED 1  /* df = sum over strata with N_++z > 0 of (values of X seen - 1)(values of Y seen - 1);
                               a test with df = 0 cannot reject (p = 1) */
 
+#define FBN_LOOP_DEVICE 0  /* the depths after any launched directly run as one CUDA graph whose while node the
+                              device drives (no host round trip between depths) */
+#define FBN_LOOP_HOST   1  /* the same kernels, one depth at a time from the host, which reads the loop flag
+                              between depths (for tools that profile kernel by kernel) */
+
 typedef struct fbn_options {
     int32_t form;        /* FBN_FORM_POOL (default) or FBN_FORM_PLAIN */
     int32_t group_size;  /* gs >= 1: consecutive conditioning sets taken per claim (Section IV-B); 0 = default (1) */
@@ -66,7 +71,8 @@ typedef struct fbn_options {
                             vertex's neighbourhood at once on the tensor cores, or the work pool */
     int32_t statistic;   /* FBN_STAT_G2 (default) or FBN_STAT_X2: the statistic of every CI test */
     int32_t df_mode;     /* FBN_DF_FIXED (default) or FBN_DF_ADJUSTED: degrees of freedom of every CI test */
-    int32_t reserved[7]; /* must be zero */
+    int32_t loop;        /* FBN_LOOP_DEVICE (default) or FBN_LOOP_HOST: who drives the depth loop */
+    int32_t reserved[6]; /* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */
@@ -79,8 +85,8 @@ typedef struct fbn_stats {
     int64_t tests[FBN_MAX_DEPTHS];          /* CI tests executed, redundant ones included */
     int64_t tests_oracle[FBN_MAX_DEPTHS];   /* tests the sequential Algorithm 1 runs (gs = 1) */
     int64_t removed[FBN_MAX_DEPTHS];        /* edges removed at depth d */
-    double  ms[FBN_MAX_DEPTHS];             /* device time of depth d (CUDA events) */
-    double  test_ms[FBN_MAX_DEPTHS];        /* device time of depth d's CI-test kernels */
+    double  ms[FBN_MAX_DEPTHS];             /* device time of depth d (device clock, ms) */
+    double  test_ms[FBN_MAX_DEPTHS];        /* device time of depth d's CI-test kernels (ms) */
     double  gram_ms;                        /* device time of the one-hot Gram (0 if not used) */
     int64_t gram_rows;                      /* M = sum of arities, when the Gram ran */
     int64_t gram_samples;                   /* padded samples of the Gram */
@@ -155,8 +161,9 @@ int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap);
  *   adj_out : uint8 [n][n], host or device, receives the symmetric 0/1
  *             adjacency of the skeleton (zero diagonal).  Nullable.
  * Separating sets stay in the handle until the next call or fbn_destroy; read
- * them with fbn_get_sepset / fbn_export_sepsets (the first such read copies
- * them from the device).
+ * them with fbn_get_sepset / fbn_export_sepsets (the first such read compacts
+ * them on the device and copies the compact form to the host; for a handle of
+ * a batch, every member's sets at once).
  * Errors: FBN_EINVAL (alpha outside (0, 1), max_depth < -1), FBN_ETOOBIG,
  * FBN_ENOMEM, FBN_ENUMERIC, FBN_ECUDA. */
 int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* adj_out);

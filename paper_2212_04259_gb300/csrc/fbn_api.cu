@@ -28,7 +28,7 @@ constexpr size_t kSmemBytes = 100 * 1024;     // dynamic shared memory of a CTA 
 constexpr long long kSplitStride = 4096;        // cells of a split test's global table at most
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
-constexpr int kCritDense = 8192;              // critical values kept densely: df < kCritDense
+constexpr int kCritDense = 8192;              // critical values kept in a dense table: df < kCritDense
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
@@ -124,6 +124,11 @@ struct Workspace {
     std::vector<uint8_t> up_last;
     uint8_t* h_up = nullptr;
     size_t h_up_cap = 0;
+    // pinned staging of the separating-set export: totals, then the arrays
+    long long* h_tot = nullptr;
+    size_t h_tot_cap = 0;
+    uint8_t* h_stage = nullptr;
+    size_t h_stage_cap = 0;
     int gram_n_units = 0;
     std::vector<uint8_t> h_maps;
     // one-hot layout of the last prepare_gram and the last one whose pad rows
@@ -154,6 +159,8 @@ struct Workspace {
         dfree(d_rec);
         if (h_rec) cudaFreeHost(h_rec);
         if (h_up) cudaFreeHost(h_up);
+        if (h_tot) cudaFreeHost(h_tot);
+        if (h_stage) cudaFreeHost(h_stage);
         h_maps.clear();
         gram_E = nullptr; gram_G = nullptr; gram_maps = nullptr; gram_units = nullptr; pk = nullptr;
         split_tab = nullptr; split_ticket = nullptr;
@@ -165,6 +172,7 @@ struct Workspace {
 struct DeviceInts {
     int32_t* d = nullptr;
     long long n = 0;
+    std::vector<fbn_handle*> members;   // the handles whose sets live here (a batch)
     ~DeviceInts()
     {
         if (d) cudaFree(d);
@@ -526,58 +534,131 @@ int run_gram(fbn_handle* h, Workspace& ws, int k, int total_vtx, unsigned* d_sta
 
 // Copy the separating sets of h (in the pool of workspace ws) to the host,
 // as CSR rows per removed pair.
+// Move a handle to another separating-set snapshot (or to none).
+void set_snapshot(fbn_handle* h, std::shared_ptr<DeviceInts> snap)
+{
+    if (h->sep_snap) {
+        auto& m = h->sep_snap->members;
+        m.erase(std::remove(m.begin(), m.end(), h), m.end());
+    }
+    h->sep_snap = std::move(snap);
+    if (h->sep_snap) h->sep_snap->members.push_back(h);
+}
+
+// Grow a pinned host buffer (contents not kept).
+template <class T>
+cudaError_t grow_pinned(T** p, size_t* cap, size_t n)
+{
+    if (n <= *cap) return cudaSuccess;
+    if (*p) cudaFreeHost(*p);
+    *p = nullptr;
+    *cap = 0;
+    const cudaError_t e = cudaMallocHost((void**)p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) *cap = n;
+    return e;
+}
+
+// The handle's separating sets as host CSR, compacted on the device; for a
+// handle of a batch every member whose sets are still on the device is
+// compacted in the same two passes (counts, then arrays), one synchronisation
+// each, through pinned staging.
 int materialize_sepsets(fbn_handle* h, Workspace& ws)
 {
     if (!h->sep_pending) return FBN_OK;
     CK(cudaSetDevice(h->device));
     cudaStream_t st = h->stream;
-    const int n = h->n;
-    // the members live in this handle's pool, or in its batch's snapshot
-    const int32_t* pool = h->sep_snap ? h->sep_snap->d : ws.sep_pool;
-    if (!h->d_sep_cnt) CK(dalloc(&h->d_sep_cnt, 4 * (size_t)n + 4));
-    long long* cnt = h->d_sep_cnt;
-    long long* roff_p = cnt + 2 * (size_t)n;
-    long long* roff_m = roff_p + n + 1;
-    CK(launch_sep_count(h->d_sep_len, n, cnt, roff_p, roff_m, st));
-    long long tot[2] = {0, 0};
-    CK(cudaMemcpyAsync(&tot[0], roff_p + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&tot[1], roff_m + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    std::vector<fbn_handle*> todo;
+    if (h->sep_snap) {
+        for (fbn_handle* q : h->sep_snap->members)
+            if (q->sep_pending && q->device == h->device) todo.push_back(q);
+    } else {
+        todo.push_back(h);
+    }
+    const size_t k = todo.size();
+    CK(grow_pinned(&ws.h_tot, &ws.h_tot_cap, 2 * k));
+    for (size_t i = 0; i < k; ++i) {   // pass 1: row counts and offsets, totals to the host
+        fbn_handle* q = todo[i];
+        const int n = q->n;
+        if (!q->d_sep_cnt) CK(dalloc(&q->d_sep_cnt, 4 * (size_t)n + 4));
+        long long* roff_p = q->d_sep_cnt + 2 * (size_t)n;
+        long long* roff_m = roff_p + n + 1;
+        CK(launch_sep_count(q->d_sep_len, n, q->d_sep_cnt, roff_p, roff_m, st));
+        CK(cudaMemcpyAsync(ws.h_tot + 2 * i, roff_p + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ws.h_tot + 2 * i + 1, roff_m + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    }
     CK(cudaStreamSynchronize(st));
-    const long long R = tot[0], Mtot = tot[1];
-    if (R > h->csr_pairs_cap) {
-        dfree(h->d_csr_pairs);
-        dfree(h->d_csr_offs);
-        h->d_csr_pairs = nullptr;
-        h->d_csr_offs = nullptr;
-        h->csr_pairs_cap = 0;
-        CK(dalloc(&h->d_csr_pairs, 2 * (size_t)R));
-        CK(dalloc(&h->d_csr_offs, (size_t)R + 1));
-        h->csr_pairs_cap = R;
+    // one handle: straight into its host arrays; a batch: through one pinned
+    // staging buffer, so that the copies of every member stay asynchronous
+    const bool staged = k > 1;
+    std::vector<size_t> at(k + 1, 0);   // staging offsets (bytes)
+    for (size_t i = 0; i < k; ++i) {
+        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
+        at[i + 1] = at[i] + (size_t)R * (2 * sizeof(int32_t) + sizeof(int64_t)) + (size_t)Mtot * sizeof(int32_t);
+        if (!staged) {
+            todo[i]->csr_pairs.resize(2 * (size_t)R);
+            todo[i]->csr_offs.resize((size_t)R + 1);
+            todo[i]->csr_members.resize((size_t)Mtot);
+        }
     }
-    if (Mtot > h->csr_members_cap) {
-        dfree(h->d_csr_members);
-        h->d_csr_members = nullptr;
-        h->csr_members_cap = 0;
-        CK(dalloc(&h->d_csr_members, (size_t)Mtot));
-        h->csr_members_cap = Mtot;
-    }
-    h->csr_pairs.resize(2 * (size_t)R);
-    h->csr_offs.resize((size_t)R + 1);
-    h->csr_members.resize((size_t)Mtot);
-    if (R > 0) {
-        CK(launch_sep_write(h->d_sep_len, h->d_sep_off, pool, n, roff_p, roff_m, h->d_csr_pairs, h->d_csr_offs,
-                            h->d_csr_members, st));
-        CK(cudaMemcpyAsync(h->csr_pairs.data(), h->d_csr_pairs, 2 * (size_t)R * sizeof(int32_t),
-                           cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(h->csr_offs.data(), h->d_csr_offs, (size_t)R * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                           st));
+    if (staged) CK(grow_pinned(&ws.h_stage, &ws.h_stage_cap, at[k]));
+    for (size_t i = 0; i < k; ++i) {   // pass 2: the compact arrays
+        fbn_handle* q = todo[i];
+        const int n = q->n;
+        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
+        if (R > q->csr_pairs_cap) {
+            dfree(q->d_csr_pairs);
+            dfree(q->d_csr_offs);
+            q->d_csr_pairs = nullptr;
+            q->d_csr_offs = nullptr;
+            q->csr_pairs_cap = 0;
+            CK(dalloc(&q->d_csr_pairs, 2 * (size_t)R));
+            CK(dalloc(&q->d_csr_offs, (size_t)R + 1));
+            q->csr_pairs_cap = R;
+        }
+        if (Mtot > q->csr_members_cap) {
+            dfree(q->d_csr_members);
+            q->d_csr_members = nullptr;
+            q->csr_members_cap = 0;
+            CK(dalloc(&q->d_csr_members, (size_t)Mtot));
+            q->csr_members_cap = Mtot;
+        }
+        if (R == 0) continue;
+        // the members live in the handle's own pool, or in its batch's snapshot
+        const int32_t* pool = q->sep_snap ? q->sep_snap->d : q->ws.sep_pool;
+        long long* roff_p = q->d_sep_cnt + 2 * (size_t)n;
+        long long* roff_m = roff_p + n + 1;
+        CK(launch_sep_write(q->d_sep_len, q->d_sep_off, pool, n, roff_p, roff_m, q->d_csr_pairs, q->d_csr_offs,
+                            q->d_csr_members, st));
+        uint8_t* dst = staged ? ws.h_stage + at[i] : nullptr;
+        void* dp = staged ? (void*)dst : (void*)q->csr_pairs.data();
+        CK(cudaMemcpyAsync(dp, q->d_csr_pairs, 2 * (size_t)R * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        void* doff = staged ? (void*)(dst + 2 * (size_t)R * sizeof(int32_t)) : (void*)q->csr_offs.data();
+        CK(cudaMemcpyAsync(doff, q->d_csr_offs, (size_t)R * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        void* dm = staged ? (void*)(dst + (size_t)R * (2 * sizeof(int32_t) + sizeof(int64_t)))
+                          : (void*)q->csr_members.data();
         if (Mtot > 0)
-            CK(cudaMemcpyAsync(h->csr_members.data(), h->d_csr_members, (size_t)Mtot * sizeof(int32_t),
-                               cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+            CK(cudaMemcpyAsync(dm, q->d_csr_members, (size_t)Mtot * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     }
-    h->csr_offs[(size_t)R] = Mtot;
-    h->sep_pending = false;
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < k; ++i) {
+        fbn_handle* q = todo[i];
+        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
+        if (staged) {
+            q->csr_pairs.resize(2 * (size_t)R);
+            q->csr_offs.resize((size_t)R + 1);
+            q->csr_members.resize((size_t)Mtot);
+        }
+        const uint8_t* src = staged ? ws.h_stage + at[i] : nullptr;
+        if (staged && R > 0) {
+            std::memcpy(q->csr_pairs.data(), src, 2 * (size_t)R * sizeof(int32_t));
+            src += 2 * (size_t)R * sizeof(int32_t);
+            std::memcpy(q->csr_offs.data(), src, (size_t)R * sizeof(int64_t));
+            src += (size_t)R * sizeof(int64_t);
+            if (Mtot > 0) std::memcpy(q->csr_members.data(), src, (size_t)Mtot * sizeof(int32_t));
+        }
+        q->csr_offs[(size_t)R] = Mtot;
+        q->sep_pending = false;
+    }
     return FBN_OK;
 }
 
@@ -696,8 +777,11 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     const long long gs_edges = 8LL * grid_small * 8;   // live edges from which 4 ranks per claim pay
     const long long wcap = plain ? 0 : warp_cells_cap();   // the plain form runs every edge on a CTA
     const int forced = h->opt.group_threads;
-    const bool new_alpha = ws.crit_alpha != alpha;
-    if (new_alpha) CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
+    if (ws.crit_alpha != alpha) {
+        CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
+        CK(cudaMemsetAsync(ws.crit_dense, 0, kCritDense * sizeof(double), st));
+        ws.crit_alpha = alpha;
+    }
     CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, kCritDense, ws.crit_dense};
 
     CK(cudaMemsetAsync(ws.d_rec, 0, kMaxDepthRecords * sizeof(DepthRecord), st));
@@ -708,11 +792,6 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     c0.rec = ws.d_rec;
     *ws.h_ctr = c0;
     CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
-    if (new_alpha) {   // after the counters: an iteration cap sets their status
-        launch_crit_fill(alpha, ws.crit_dense, kCritDense, &ws.d_ctr->status, st);
-        CK(cudaGetLastError());
-        launches += 1;
-    }
 
     PoolArgs base{};
     base.probs = ws.probs;
@@ -918,7 +997,22 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         d_loop = 2;
     }
     const bool loop = max_depth < 0 || d_loop <= max_depth;
-    if (loop) {
+    const bool host_loop = h->opt.loop == FBN_LOOP_HOST;
+    if (loop && host_loop) {
+        // the same kernels, depth by depth: the edge list, then while the
+        // depth has an edge to test, its tests, removal and end, and the next
+        // depth's edge list
+        enqueue_head();
+        launches += 2;
+        for (;;) {
+            CK(cudaMemcpyAsync(ws.h_ctr, ws.d_ctr, sizeof(DepthCounters), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (!ws.h_ctr->active || ws.h_ctr->n_edges[0] + ws.h_ctr->n_edges[1] == 0) break;
+            enqueue_tests();
+            enqueue_tail();
+            enqueue_head();
+        }
+    } else if (loop) {
         CK(cudaGraphLaunch(ws.loop, st));
         launches += 3;
     }
@@ -930,7 +1024,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             if (adj_out[p])
                 CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, (size_t)hs[p]->n * hs[p]->n, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
-    if (loop) launches += (long long)body_launches * std::max(0, ws.h_ctr->d - d_loop);
+    if (loop) launches += (long long)(body_launches - (host_loop ? 1 : 0)) * std::max(0, ws.h_ctr->d - d_loop);
     for (int q = 0; q < 2; ++q)
         if (direct[q]) {
             float kms = 0.f;
@@ -955,7 +1049,6 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     }
     rc = check_status(h, c.status);
     if (rc) return rc;
-    ws.crit_alpha = alpha;   // the dense critical values are complete for this alpha
 
     for (int d = 0; d < kMaxDepthRecords; ++d) {
         const DepthRecord& r = ws.h_rec[d];
@@ -998,7 +1091,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         hs[p]->learnt = true;
         hs[p]->sep_pending = true;
         hs[p]->sep_pool_used = c.sep_used;
-        hs[p]->sep_snap = snap;
+        set_snapshot(hs[p], snap);
     }
     return FBN_OK;
 }
@@ -1077,6 +1170,7 @@ void free_handle(fbn_handle* h)
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    set_snapshot(h, nullptr);
     h->ws.release();
     dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
@@ -1114,8 +1208,9 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 7; ++k)
+        for (int k = 0; k < 6; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
+        if (o.loop != FBN_LOOP_DEVICE && o.loop != FBN_LOOP_HOST) return fail(nullptr, FBN_EINVAL, "bad loop %d", o.loop);
         if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
         if (o.group_threads != 0 && o.group_threads != 32 && o.group_threads != 64 && o.group_threads != 128 &&
             o.group_threads != kTestThreads)

@@ -20,8 +20,9 @@ namespace fbn {
 // Chi-square survival function Q(df/2, g2/2) in FP64.
 // Series for the lower regularised gamma P (Abramowitz & Stegun 6.5.29) when
 // x < a + 1, else the continued fraction for the upper one (A&S 6.5.31)
-// evaluated with the modified Lentz method.  lgamma/log/exp are CUDA's.
-__device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status)
+// evaluated with the modified Lentz method.  lgamma/log/exp are CUDA's.  An
+// iteration cap sets kStatusNumeric in *status (and *capped when given).
+__device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status, bool* capped = nullptr)
 {
     if (!(g2 > 0.0)) return 1.0;
     const double a = 0.5 * df, x = 0.5 * g2;
@@ -37,7 +38,10 @@ __device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status
             sum += term;
             if (term < sum * kEps) break;
         }
-        if (it == kMaxIt) atomicOr(status, kStatusNumeric);
+        if (it == kMaxIt) {
+            atomicOr(status, kStatusNumeric);
+            if (capped) *capped = true;
+        }
         const double q = 1.0 - sum * exp(log_pref);
         return q < 0.0 ? 0.0 : q;
     }
@@ -55,7 +59,10 @@ __device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status
         h *= del;
         if (fabs(del - 1.0) < kEps) break;
     }
-    if (i == kMaxIt) atomicOr(status, kStatusNumeric);
+    if (i == kMaxIt) {
+        atomicOr(status, kStatusNumeric);
+        if (capped) *capped = true;
+    }
     const double q = exp(log_pref) * h;
     return q > 1.0 ? 1.0 : q;
 }
@@ -64,17 +71,17 @@ __device__ __forceinline__ double chisq_q(double df, double g2, unsigned* status
 // strictly decreasing in G^2, so "p > alpha" is exactly "G^2 < crit".  Found
 // by a safeguarded Newton iteration inside a bracket [lo, hi] with Q(lo) >
 // alpha >= Q(hi); the derivative of Q in G^2 is minus the chi-square density.
-__device__ __forceinline__ double chisq_crit(double df, double alpha, unsigned* status)
+__device__ __forceinline__ double chisq_crit(double df, double alpha, unsigned* status, bool* capped = nullptr)
 {
     const double a = 0.5 * df;
     double lo = 0.0, hi = df + 10.0 * sqrt(2.0 * df) + 40.0;
-    for (int k = 0; k < 64 && chisq_q(df, hi, status) > alpha; ++k) {
+    for (int k = 0; k < 64 && chisq_q(df, hi, status, capped) > alpha; ++k) {
         lo = hi;
         hi *= 2.0;
     }
     double x = 0.5 * (lo + hi);
     for (int it = 0; it < 200; ++it) {
-        const double q = chisq_q(df, x, status);
+        const double q = chisq_q(df, x, status, capped);
         if (q > alpha) lo = x; else hi = x;
         // density of chi^2_df at x: x^{a-1} e^{-x/2} / (2^a Gamma(a))
         const double lpdf = (a - 1.0) * log(x) - 0.5 * x - a * 0.6931471805599453 - lgamma(a);
@@ -90,11 +97,13 @@ __device__ __forceinline__ double chisq_crit(double df, double alpha, unsigned* 
     return x;
 }
 
-// Critical values for one alpha: a dense table for small df (filled by a
-// kernel before the depth loop, read-only while it runs), then an
-// open-addressing cache keyed by df.  A cache slot is claimed with a CAS to
-// -1, filled, then published with a release store of the key; readers that
-// see -1 compute the value themselves, so no thread ever waits on another.
+// Critical values for one alpha.  Small df: a dense table whose slot holds 0
+// until a test computes the value and stores it (the value is its own
+// payload: a reader sees 0 or the value, and one that sees 0 computes it
+// too; a value whose computation hit an iteration cap is never stored).
+// Larger df: an open-addressing cache keyed by df; a slot is claimed with a
+// CAS to -1, filled, then published with a release store of the key; readers
+// that see -1 compute the value themselves.  No thread waits on another.
 using CritTable = CritTableDev;
 
 __device__ __forceinline__ long long ld_acquire(const long long* p)
@@ -111,7 +120,14 @@ __device__ __forceinline__ void st_release(long long* p, long long v)
 
 __device__ __forceinline__ double crit_get(const CritTable& t, long long df, double alpha, unsigned* status)
 {
-    if (df < t.dense_n) return __ldg(t.dense + df);
+    if (df < t.dense_n) {
+        const double v = t.dense[df];
+        if (v > 0.0) return v;
+        bool capped = false;
+        const double c = chisq_crit((double)df, alpha, status, &capped);
+        if (!capped) t.dense[df] = c;
+        return c;
+    }
     unsigned h = (unsigned)(df * 0x9E3779B97F4A7C15ULL >> 40) & (unsigned)(t.cap - 1);
     for (int probe = 0; probe < 32; ++probe, h = (h + 1) & (unsigned)(t.cap - 1)) {
         const long long k = ld_acquire(t.keys + h);

@@ -138,8 +138,8 @@ struct CritTableDev {
     long long* keys;
     double* vals;
     int cap;
-    int dense_n;           // df < dense_n: dense[df], filled before the depth loop
-    const double* dense;
+    int dense_n;           // df < dense_n: dense[df], 0 until a test computes it
+    double* dense;
 };
 
 // Work pool of one depth and one edge class.  Sizes, the depth and the class

@@ -780,14 +780,6 @@ __global__ void k_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop)
     cudaGraphSetConditional(loop, go ? 1u : 0u);
 }
 
-// Dense critical values crit[df] for 1 <= df < n (crit[0] unused).
-__global__ void k_crit_fill(double alpha, double* __restrict__ dense, int n, unsigned* status)
-{
-    const int df = blockIdx.x * blockDim.x + threadIdx.x;
-    if (df >= n) return;
-    dense[df] = df == 0 ? 0.0 : chisq_crit((double)df, alpha, status);
-}
-
 // --------------------------------------------------------------------------
 // Explicit tests (fbn_ci_test / fbn_ci_table): exact FP64 G^2 and p-value.
 __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __restrict__ prob,
@@ -928,11 +920,6 @@ void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream
 void set_pdl(bool on)
 {
     g_pdl = on;
-}
-
-void launch_crit_fill(double alpha, double* dense, int n, unsigned* status, cudaStream_t st)
-{
-    k_crit_fill<<<(n + 127) / 128, 128, 0, st>>>(alpha, dense, n, status);
 }
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,

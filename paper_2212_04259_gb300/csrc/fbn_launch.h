@@ -38,8 +38,6 @@ void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsig
 void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream_t st);
 // Programmatic dependent launch for the depth kernels (on by default).
 void set_pdl(bool on);
-// Critical values of the chi-square test at level alpha for df < n.
-void launch_crit_fill(double alpha, double* dense, int n, unsigned* status, cudaStream_t st);
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
                      size_t smem_bytes, int stat, int df_mode, cudaStream_t st);

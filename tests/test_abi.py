@@ -72,6 +72,12 @@ def test_create_rejects_bad_arguments_before_touching_a_device(built):
     with pytest.raises(f.FbnError) as e:
         f.fbn_create(np.zeros((2, 10), np.uint8), [2, 2], depth0="gram", form="pool", group_threads=48)
     assert e.value.code == -1
+    o = f.fbn.Options(device=-1, loop=2)                     # neither loop driver
+    out = f.fbn.C.c_void_p()
+    data = np.zeros((2, 10), np.uint8)
+    ar = np.array([2, 2], np.uint8)
+    rc = f.fbn.lib().fbn_create(f.fbn._ptr(data), 2, 10, f.fbn._ptr(ar), f.fbn.C.byref(o), f.fbn.C.byref(out))
+    assert rc == -1 and "bad loop" in f.fbn_last_error(None)
 
 
 def test_no_cpu_fallback_without_gpu(built):
