@@ -226,12 +226,8 @@ struct fbn_handle {
     std::vector<int32_t> csr_pairs;
     std::vector<int64_t> csr_offs;
     std::vector<int32_t> csr_members;
-    // device side of the compaction, grown as needed
-    long long* d_sep_cnt = nullptr;     // [2n] row counts, then [2][n + 1] row offsets
-    int32_t* d_csr_pairs = nullptr;
-    int64_t* d_csr_offs = nullptr;
-    int32_t* d_csr_members = nullptr;
-    long long csr_pairs_cap = 0, csr_members_cap = 0;
+    // row counts of the compaction on the device: [2n] counts, then [2][n + 1] row offsets
+    long long* d_sep_cnt = nullptr;
     fbn_stats stats{};
     Workspace ws;
     std::string err;
@@ -558,10 +554,13 @@ cudaError_t grow_pinned(T** p, size_t* cap, size_t n)
     return e;
 }
 
-// The handle's separating sets as host CSR, compacted on the device; for a
-// handle of a batch every member whose sets are still on the device is
-// compacted in the same two passes (counts, then arrays), one synchronisation
-// each, through pinned staging.
+// The handle's separating sets as host CSR, compacted on the device by a
+// kernel that writes the compact arrays straight into pinned host staging
+// (device-addressable). One handle: staging sized by bounds known on the
+// host (every pair removed; every pool entry its own), one synchronisation.
+// A handle of a batch: every member whose sets are still on the device, in
+// two passes (row counts and totals; then the arrays), one synchronisation
+// each.
 int materialize_sepsets(fbn_handle* h, Workspace& ws)
 {
     if (!h->sep_pending) return FBN_OK;
@@ -575,90 +574,82 @@ int materialize_sepsets(fbn_handle* h, Workspace& ws)
         todo.push_back(h);
     }
     const size_t k = todo.size();
-    CK(grow_pinned(&ws.h_tot, &ws.h_tot_cap, 2 * k));
-    for (size_t i = 0; i < k; ++i) {   // pass 1: row counts and offsets, totals to the host
-        fbn_handle* q = todo[i];
+    auto align16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    // staging of one handle laid out for L pairs: pairs int32 [2L], offsets
+    // int64 [L], members int32
+    auto place = [](uint8_t* base, long long L, int32_t** pr, int64_t** of, int32_t** mb) {
+        *pr = reinterpret_cast<int32_t*>(base);
+        *of = reinterpret_cast<int64_t*>(base + 2 * (size_t)L * sizeof(int32_t));
+        *mb = reinterpret_cast<int32_t*>(base + (size_t)L * (2 * sizeof(int32_t) + sizeof(int64_t)));
+    };
+    auto count = [&](fbn_handle* q, long long* tot) -> int {
         const int n = q->n;
         if (!q->d_sep_cnt) CK(dalloc(&q->d_sep_cnt, 4 * (size_t)n + 4));
         long long* roff_p = q->d_sep_cnt + 2 * (size_t)n;
         long long* roff_m = roff_p + n + 1;
         CK(launch_sep_count(q->d_sep_len, n, q->d_sep_cnt, roff_p, roff_m, st));
-        CK(cudaMemcpyAsync(ws.h_tot + 2 * i, roff_p + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(ws.h_tot + 2 * i + 1, roff_m + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    // one handle: straight into its host arrays; a batch: through one pinned
-    // staging buffer, so that the copies of every member stay asynchronous
-    const bool staged = k > 1;
-    std::vector<size_t> at(k + 1, 0);   // staging offsets (bytes)
-    for (size_t i = 0; i < k; ++i) {
-        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
-        at[i + 1] = at[i] + (size_t)R * (2 * sizeof(int32_t) + sizeof(int64_t)) + (size_t)Mtot * sizeof(int32_t);
-        if (!staged) {
-            todo[i]->csr_pairs.resize(2 * (size_t)R);
-            todo[i]->csr_offs.resize((size_t)R + 1);
-            todo[i]->csr_members.resize((size_t)Mtot);
-        }
-    }
-    if (staged) CK(grow_pinned(&ws.h_stage, &ws.h_stage_cap, at[k]));
-    for (size_t i = 0; i < k; ++i) {   // pass 2: the compact arrays
-        fbn_handle* q = todo[i];
+        CK(cudaMemcpyAsync(tot, roff_p + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(tot + 1, roff_m + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        return FBN_OK;
+    };
+    auto write = [&](fbn_handle* q, uint8_t* base, long long L) -> int {
         const int n = q->n;
-        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
-        if (R > q->csr_pairs_cap) {
-            dfree(q->d_csr_pairs);
-            dfree(q->d_csr_offs);
-            q->d_csr_pairs = nullptr;
-            q->d_csr_offs = nullptr;
-            q->csr_pairs_cap = 0;
-            CK(dalloc(&q->d_csr_pairs, 2 * (size_t)R));
-            CK(dalloc(&q->d_csr_offs, (size_t)R + 1));
-            q->csr_pairs_cap = R;
-        }
-        if (Mtot > q->csr_members_cap) {
-            dfree(q->d_csr_members);
-            q->d_csr_members = nullptr;
-            q->csr_members_cap = 0;
-            CK(dalloc(&q->d_csr_members, (size_t)Mtot));
-            q->csr_members_cap = Mtot;
-        }
-        if (R == 0) continue;
-        // the members live in the handle's own pool, or in its batch's snapshot
         const int32_t* pool = q->sep_snap ? q->sep_snap->d : q->ws.sep_pool;
         long long* roff_p = q->d_sep_cnt + 2 * (size_t)n;
         long long* roff_m = roff_p + n + 1;
-        CK(launch_sep_write(q->d_sep_len, q->d_sep_off, pool, n, roff_p, roff_m, q->d_csr_pairs, q->d_csr_offs,
-                            q->d_csr_members, st));
-        uint8_t* dst = staged ? ws.h_stage + at[i] : nullptr;
-        void* dp = staged ? (void*)dst : (void*)q->csr_pairs.data();
-        CK(cudaMemcpyAsync(dp, q->d_csr_pairs, 2 * (size_t)R * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        void* doff = staged ? (void*)(dst + 2 * (size_t)R * sizeof(int32_t)) : (void*)q->csr_offs.data();
-        CK(cudaMemcpyAsync(doff, q->d_csr_offs, (size_t)R * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        void* dm = staged ? (void*)(dst + (size_t)R * (2 * sizeof(int32_t) + sizeof(int64_t)))
-                          : (void*)q->csr_members.data();
-        if (Mtot > 0)
-            CK(cudaMemcpyAsync(dm, q->d_csr_members, (size_t)Mtot * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    for (size_t i = 0; i < k; ++i) {
-        fbn_handle* q = todo[i];
-        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
-        if (staged) {
-            q->csr_pairs.resize(2 * (size_t)R);
-            q->csr_offs.resize((size_t)R + 1);
-            q->csr_members.resize((size_t)Mtot);
-        }
-        const uint8_t* src = staged ? ws.h_stage + at[i] : nullptr;
-        if (staged && R > 0) {
-            std::memcpy(q->csr_pairs.data(), src, 2 * (size_t)R * sizeof(int32_t));
-            src += 2 * (size_t)R * sizeof(int32_t);
-            std::memcpy(q->csr_offs.data(), src, (size_t)R * sizeof(int64_t));
-            src += (size_t)R * sizeof(int64_t);
-            if (Mtot > 0) std::memcpy(q->csr_members.data(), src, (size_t)Mtot * sizeof(int32_t));
-        }
-        q->csr_offs[(size_t)R] = Mtot;
+        int32_t* pr = nullptr;
+        int64_t* of = nullptr;
+        int32_t* mb = nullptr;
+        place(base, L, &pr, &of, &mb);
+        CK(launch_sep_write(q->d_sep_len, q->d_sep_off, pool, n, roff_p, roff_m, pr, of, mb, st));
+        return FBN_OK;
+    };
+    auto unpack = [&](fbn_handle* q, uint8_t* base, long long L, long long R, long long Mtot) {
+        int32_t* pr = nullptr;
+        int64_t* of = nullptr;
+        int32_t* mb = nullptr;
+        place(base, L, &pr, &of, &mb);
+        q->csr_pairs.assign(pr, pr + 2 * (size_t)R);
+        q->csr_offs.assign(of, of + (size_t)R);
+        q->csr_offs.push_back(Mtot);
+        q->csr_members.assign(mb, mb + (size_t)Mtot);
         q->sep_pending = false;
+    };
+    int rc = FBN_OK;
+    if (k == 1) {
+        fbn_handle* q = todo[0];
+        const long long Rmax = (long long)q->n * (q->n - 1) / 2;
+        const long long Mmax = (long long)q->sep_pool_used;
+        const size_t bytes = align16((size_t)Rmax * (2 * sizeof(int32_t) + sizeof(int64_t)) +
+                                     (size_t)Mmax * sizeof(int32_t));
+        CK(grow_pinned(&ws.h_stage, &ws.h_stage_cap, bytes + 16));
+        uint8_t* dstage = nullptr;   // the staging as the device addresses it
+        CK(cudaHostGetDevicePointer((void**)&dstage, ws.h_stage, 0));
+        long long* tot = reinterpret_cast<long long*>(ws.h_stage + bytes);
+        if ((rc = count(q, tot)) || (rc = write(q, dstage, Rmax))) return rc;
+        CK(cudaStreamSynchronize(st));
+        if (tot[0] > Rmax || tot[1] > Mmax) return fail(h, FBN_ECUDA, "separating-set export over its bounds");
+        unpack(q, ws.h_stage, Rmax, tot[0], tot[1]);
+        return FBN_OK;
     }
+    CK(grow_pinned(&ws.h_tot, &ws.h_tot_cap, 2 * k));
+    for (size_t i = 0; i < k; ++i)   // pass 1: row counts and offsets, totals to the host
+        if ((rc = count(todo[i], ws.h_tot + 2 * i))) return rc;
+    CK(cudaStreamSynchronize(st));
+    std::vector<size_t> at(k + 1, 0);   // staging offsets (bytes, 16-aligned)
+    for (size_t i = 0; i < k; ++i) {
+        const long long R = ws.h_tot[2 * i], Mtot = ws.h_tot[2 * i + 1];
+        at[i + 1] = at[i] + align16((size_t)R * (2 * sizeof(int32_t) + sizeof(int64_t)) +
+                                    (size_t)Mtot * sizeof(int32_t));
+    }
+    CK(grow_pinned(&ws.h_stage, &ws.h_stage_cap, std::max<size_t>(at[k], 16)));
+    uint8_t* dstage = nullptr;
+    CK(cudaHostGetDevicePointer((void**)&dstage, ws.h_stage, 0));
+    for (size_t i = 0; i < k; ++i)   // pass 2: the compact arrays into the staging
+        if (ws.h_tot[2 * i] > 0 && (rc = write(todo[i], dstage + at[i], ws.h_tot[2 * i]))) return rc;
+    CK(cudaStreamSynchronize(st));
+    for (size_t i = 0; i < k; ++i)
+        unpack(todo[i], ws.h_stage + at[i], ws.h_tot[2 * i], ws.h_tot[2 * i], ws.h_tot[2 * i + 1]);
     return FBN_OK;
 }
 
@@ -723,7 +714,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         if (rc) return rc;
     }
     {   // problem descriptors and vertex maps: uploaded only when they changed
-        const size_t b0 = k * sizeof(ProblemDev), b1 = total_vtx * sizeof(int32_t), b2 = k * sizeof(int32_t);
+        const size_t nk = (size_t)std::max(k, 1), nv = (size_t)std::max(total_vtx, 0);
+        const size_t b0 = nk * sizeof(ProblemDev), b1 = nv * sizeof(int32_t), b2 = nk * sizeof(int32_t);
         const void* dst[3] = {ws.probs, ws.vtx_prob, ws.vtx_first};
         std::vector<uint8_t> blob(sizeof dst + b0 + b1 + b2);
         std::memcpy(blob.data(), dst, sizeof dst);
@@ -1174,7 +1166,7 @@ void free_handle(fbn_handle* h)
     h->ws.release();
     dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
-    dfree(h->d_sep_cnt); dfree(h->d_csr_pairs); dfree(h->d_csr_offs); dfree(h->d_csr_members);
+    dfree(h->d_sep_cnt);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
     dfree(h->d_off);
     if (h->h_ci) cudaFreeHost(h->h_ci);

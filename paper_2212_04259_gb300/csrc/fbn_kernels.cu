@@ -21,9 +21,11 @@
 //                the conditioning set of the lowest accepting rank
 //   k_depth_end  records the depth, decides whether Algorithm 1 goes on and
 //                clears the per-depth counters for the next depth
-// Every kernel reads the depth and the sizes from the device counters, so the
-// host can queue depth d+1 before depth d has finished; a depth queued after
-// the loop ended finds active == 0 and does nothing.
+//   k_gate       the loop's condition after the next depth's edge list
+// Every kernel reads the depth and the sizes from the device counters, so one
+// captured sequence serves every depth (the body of the depth loop's while
+// node); a kernel that runs after the loop ended finds active == 0 and does
+// nothing.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -881,7 +883,7 @@ void launch_order(const EdgeWork* edges, long long edge_cap, int nclass, DepthCo
                   unsigned long long* cursor0, unsigned long long* cursor1, int32_t* sorted, double mean_n,
                   int forced_group, long long split_stride, int allow_split, int grid, cudaStream_t st)
 {
-    launch_pdl(k_scan, dim3(nclass), dim3(1024), 0, st, sc[0], sc[nclass > 1 ? 1 : 0], ctr, mean_n, forced_group,
+    launch_pdl(k_scan, dim3(nclass), dim3(256), 0, st, sc[0], sc[nclass > 1 ? 1 : 0], ctr, mean_n, forced_group,
                split_stride, allow_split);
     launch_pdl(k_place, dim3(grid), dim3(256), 0, st, edges, edge_cap, nclass, ctr, (const unsigned long long*)sc[0].alive,
                cursor0, (const unsigned long long*)sc[nclass > 1 ? 1 : 0].alive, cursor1, sorted);

@@ -1,6 +1,7 @@
 // fbn_sepsets.cu -- the separating sets of a learnt skeleton (Algorithm 1,
 // SepSet) compacted on the device into CSR form: the removed pairs i < j in
-// ascending (i, j), one offset per pair, the members in pair order.  Only the
+// ascending (i, j), one offset per pair, the members in pair order.  The
+// writer's outputs may be pinned host memory (device-addressable): only the
 // compact arrays cross to the host.
 #include <cstdint>
 #include <cuda_runtime.h>
