@@ -122,11 +122,6 @@ __device__ __forceinline__ void onehot_lut(int v, uint32_t& lo, uint32_t& hi)
     hi = v >= 4 && v < 8 ? 0x38u << (8 * (v - 4)) : 0u;
 }
 
-__device__ __forceinline__ void st_tile(uint8_t* tile, int row, int chunk, const uint4& v)
-{
-    *reinterpret_cast<uint4*>(tile + row * 128 + ((chunk ^ (row & 7)) << 4)) = v;
-}
-
 // Bounded wait taken by every lane of a warp, with one outcome for the warp.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* status,
                                           unsigned limit)
