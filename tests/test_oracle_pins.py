@@ -264,8 +264,10 @@ def test_max_depth_stops():
 
 
 # ------------------------------------------------------------- brute-force PC-stable
-def _py_pc_stable(data, ar, alpha):
-    """Independent tiny PC-stable: numpy counts, per-stratum G^2 in mpmath, scipy p."""
+def _py_pc_stable(data, ar, alpha, edge_order_seed=None):
+    """Independent tiny PC-stable: numpy counts, per-stratum G^2 in mpmath, scipy p.
+    With edge_order_seed, the edges of each depth are tested in a random order
+    (every edge reads the same snapshot, as the edge-parallel form does)."""
     n = data.shape[0]
     adj = np.ones((n, n), dtype=bool)
     np.fill_diagonal(adj, False)
@@ -288,21 +290,22 @@ def _py_pc_stable(data, ar, alpha):
         if not any(len(a[i]) - 1 >= d for i in range(n) for _ in a[i]):
             break
         rm = []
-        for i in range(n):
-            for j in a[i]:
-                if j <= i:
-                    continue
-                done = False
-                for side in ((i, j), (j, i))[: 1 if d == 0 else 2]:
-                    cand = [v for v in a[side[0]] if v != side[1]]
-                    for S in itertools.combinations(cand, d):
-                        if test(i, j, list(S)) > alpha:
-                            rm.append((i, j))
-                            sep[(i, j)] = tuple(S)
-                            done = True
-                            break
-                    if done:
+        pairs = [(i, j) for i in range(n) for j in a[i] if j > i]
+        if edge_order_seed is not None:
+            order = np.random.default_rng(edge_order_seed + d).permutation(len(pairs))
+            pairs = [pairs[k] for k in order]
+        for i, j in pairs:
+            done = False
+            for side in ((i, j), (j, i))[: 1 if d == 0 else 2]:
+                cand = [v for v in a[side[0]] if v != side[1]]
+                for S in itertools.combinations(cand, d):
+                    if test(i, j, list(S)) > alpha:
+                        rm.append((i, j))
+                        sep[(i, j)] = tuple(S)
+                        done = True
                         break
+                if done:
+                    break
         for i, j in rm:
             adj[i, j] = adj[j, i] = False
         d += 1
@@ -318,3 +321,15 @@ def test_skeleton_matches_brute_force(seed):
         pytest.skip("near-alpha tie in this draw")
     assert np.array_equal(r.adj, adj)
     assert r.sepsets == sep
+
+
+def test_edge_parallel_form_equals_the_sequential_oracle():
+    # PC-stable (Algorithm 1): the edges of a depth read one snapshot, so any
+    # order of testing them -- the edge-parallel form -- gives the oracle's result
+    data, ar, _ = bnsynth.make_dataset(1010, 7, 8, 3, (2, 3), 0.7, 3000)
+    r = oracle.pc_stable(data, ar, 0.05)
+    if r.near:
+        pytest.skip("near-alpha tie in this draw")
+    for order_seed in (11, 12):
+        adj, sep = _py_pc_stable(data, ar, 0.05, edge_order_seed=order_seed)
+        assert np.array_equal(r.adj, adj) and r.sepsets == sep
