@@ -3,11 +3,14 @@
 
 One step = one whole skeleton (every depth: snapshot, edge list, CI tests,
 removal) of the workload, through the C ABI, with the data already resident in
-HBM.  Throughput counts the tests the sequential Algorithm 1 runs (redundant
-tests of the parallel pool are not counted).  The L2 is flushed (a 256 MB
-device write) before every timed step, outside its events.
+HBM.  The default workload is the batched one: 256 independent PC-stable
+problems (20-300 variables, 1k-50k samples) learnt together, one work-pool
+launch per depth over every problem's edges.  Throughput counts the tests the
+sequential Algorithm 1 runs (redundant tests of the parallel pool are not
+counted).  The L2 is flushed (a 256 MB device write) before every timed step,
+outside its events.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload mid|small|large|depth0|batched]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload batched|mid|small|large|depth0]
                     [--form pool|plain] [--gs G] [--impl ours|reference]
 
 Under torchrun each rank runs an independent replica of the workload on its
@@ -67,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="mid")
+    ap.add_argument("--workload", default="batched")
     ap.add_argument("--form", choices=["pool", "plain"], default="pool")
     ap.add_argument("--gs", type=int, default=0)
     ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
@@ -84,6 +87,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="host processes of the oracle baseline (0: every host core, at most 16)")
     return ap.parse_args()
 
 
@@ -171,11 +176,45 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- oracle baseline
-def oracle_rate(w, stats, budget_s=10.0, max_depths=None):
+def host_procs(args):
+    """Host processes of the oracle legs: every core, at most 16, unless pinned."""
+    return args.cpu_procs or max(1, min(16, os.cpu_count() or 1))
+
+
+def _oracle_skeleton(job):
+    """Worker of the host-core pool: one whole sequential oracle skeleton."""
+    import oracle
+    data, ar, alpha, md = job
+    return oracle.pc_stable(data, ar, alpha, md).n_tests
+
+
+def oracle_batch(w, problems, procs):
+    """Whole oracle skeletons of the given problems of a batch, one problem per
+    host process at a time (a spawned pool: no process is forked after CUDA
+    initialised); returns (oracle tests, wall seconds)."""
+    import multiprocessing as mp
+    jobs = sorted(problems, key=lambda p: -w["probs"][p][0].size)   # largest first: an even end
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_skeleton, [(w["probs"][0][0][:, :64], w["probs"][0][1], w["alpha"], 0)] * procs)
+        t0 = time.perf_counter()
+        tests = sum(pool.map(_oracle_skeleton, [(w["probs"][p][0], w["probs"][p][1], w["alpha"], w["max_depth"])
+                                                for p in jobs], chunksize=1))
+        return tests, time.perf_counter() - t0
+
+
+def oracle_rate(w, stats, args, budget_s=10.0):
     """Time the CPU oracle on a bounded sample of the workload; returns dict."""
     import numpy as np
     import oracle
-    if w["kind"] == "single" and w["data"].shape[0] <= 64:
+    if w["kind"] == "batch":
+        # every fourth problem (64 of 256, all sizes), whole skeletons
+        sample = list(range(0, len(w["probs"]), 4))
+        procs = host_procs(args)
+        tests, secs = oracle_batch(w, sample, procs)
+        return {"value": tests / secs, "unit": "tests/s", "cores": procs, "kind": "oracle",
+                "sample": f"whole sequential skeletons of every fourth problem of the batch ({len(sample)} "
+                          f"problems, {tests} oracle tests, {secs:.1f} s wall), one problem per host process"}
+    if w["data"].shape[0] <= 64:
         # the whole skeleton, repeated until the budget is used
         t0 = time.perf_counter()
         tests, runs = 0, 0
@@ -189,10 +228,7 @@ def oracle_rate(w, stats, budget_s=10.0, max_depths=None):
         return {"value": tests / dt, "unit": "tests/s", "cores": 1, "kind": "oracle",
                 "sample": f"{runs} full sequential skeletons of the workload ({tests // runs} tests each)"}
     # per-depth sample: random tests of the right size, weighted by the GPU's oracle-equivalent counts
-    if w["kind"] == "single":
-        sets = [(w["data"], w["ar"])]
-    else:
-        sets = w["probs"][:16]
+    data, ar = w["data"], w["ar"]
     rng = np.random.default_rng(0)
     per_depth = stats["tests_oracle"]
     total = sum(per_depth)
@@ -206,7 +242,6 @@ def oracle_rate(w, stats, budget_s=10.0, max_depths=None):
         t0 = time.perf_counter()
         k = 0
         while True:
-            data, ar = sets[k % len(sets)]
             v = rng.permutation(data.shape[0])[: d + 2]
             oracle.ci_test(data, ar, int(v[0]), int(v[1]), [int(t) for t in v[2:]])
             k += 1
@@ -222,33 +257,40 @@ def oracle_rate(w, stats, budget_s=10.0, max_depths=None):
 
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, w, name, rank, world):
+    """The reference arm: this tier's reference program is the CPU oracle,
+    timed as it stands on the host cores (rank 0 only)."""
     if rank != 0:
         return
-    import oracle  # the CPU oracle is this tier's reference program
+    import oracle
     oracle.build()
-    import numpy as np
-    # a bounded sample per step: the whole small skeletons, else 2 s of sampled tests
-    def one_step():
-        if w["kind"] == "single" and w["data"].shape[0] <= 64:
+    procs = host_procs(args) if w["kind"] == "batch" else 1
+
+    def one_step(k):
+        if w["kind"] == "batch":
+            # a sixteenth of the batch per step (problems p = k mod 16), whole skeletons
+            probs = [p for p in range(len(w["probs"])) if p % 16 == k % 16]
+            t, s = oracle_batch(w, probs, procs)
+            return t, s, "a sixteenth of the batch per step (problems p = step mod 16, 16 problems), whole " \
+                         "sequential skeletons, one problem per host process"
+        if w["data"].shape[0] <= 64:
             t0 = time.perf_counter()
             r = oracle.pc_stable(w["data"], w["ar"], w["alpha"], w["max_depth"])
             return r.n_tests, time.perf_counter() - t0, "one full sequential skeleton per step"
-        sets = [(w["data"], w["ar"])] if w["kind"] == "single" else w["probs"][:16]
-        rng = np.random.default_rng(1)
+        import numpy as np
+        rng = np.random.default_rng(1 + k)
         t0 = time.perf_counter()
-        k = 0
+        n = 0
         while time.perf_counter() - t0 < 2.0:
-            data, ar = sets[k % len(sets)]
             d = int(rng.integers(0, 3))
-            v = rng.permutation(data.shape[0])[: d + 2]
-            oracle.ci_test(data, ar, int(v[0]), int(v[1]), [int(t) for t in v[2:]])
-            k += 1
-        return k, time.perf_counter() - t0, "2 s of sampled single CI tests (depths 0-2) per step"
-    for _ in range(args.warmup):
-        one_step()
+            v = rng.permutation(w["data"].shape[0])[: d + 2]
+            oracle.ci_test(w["data"], w["ar"], int(v[0]), int(v[1]), [int(t) for t in v[2:]])
+            n += 1
+        return n, time.perf_counter() - t0, "2 s of sampled single CI tests (depths 0-2) per step"
+    for k in range(args.warmup):
+        one_step(k)
     tests, secs, what = 0, 0.0, ""
-    for _ in range(args.steps):
-        t, s, what = one_step()
+    for k in range(args.steps):
+        t, s, what = one_step(args.warmup + k)
         tests += t
         secs += s
     val = tests / secs
@@ -256,7 +298,7 @@ def run_reference(args, w, name, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(name, w, args),
-            "cpu_baseline": {"value": val, "unit": "tests/s", "cores": 1, "kind": "oracle", "sample": what},
+            "cpu_baseline": {"value": val, "unit": "tests/s", "cores": procs, "kind": "oracle", "sample": what},
             "e2e": {"value": val, "unit": "tests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -419,19 +461,15 @@ def main():
     value = job_throughput(tests, ms, world)
 
     # rooflines.  Histogram test kernels (the work pool): algorithmic sample
-    # bytes (d + 2) N per oracle-equivalent test over their CUDA-event time,
-    # against the measured HBM copy bandwidth.  Depth 0 on the one-hot Gram:
-    # algorithmic FLOPs 2 * M^2 * N / 2 (upper triangle, M = sum of arities)
-    # over the Gram kernel's time, against the FP8 dense peak (the measured
-    # bf16 peak times the nominal FP8/BF16 ratio of 2).
-    if w["kind"] == "single":
-        Ns = [w["data"].shape[1]]
-    else:
-        Ns = [d.shape[1] for d, _ in w["probs"]]
-    meanN = sum(Ns) / len(Ns)
+    # bytes (d + 2) N per oracle-equivalent test -- each test weighted by its
+    # own problem's N (the library sums N over each depth's tests) -- over
+    # their device time, against the measured HBM copy bandwidth.  Depth 0 on
+    # the one-hot Gram: algorithmic FLOPs 2 * M^2 * N / 2 (upper triangle,
+    # M = sum of arities) over the Gram kernel's time, against the FP8 dense
+    # peak (the measured bf16 peak times the nominal FP8/BF16 ratio of 2).
     gram_used = st["gram_ms"] > 0
     pool_depths = [d for d in range(st["depths"]) if not (gram_used and d == 0)]
-    alg_bytes = sum(st["tests_oracle"][d] * (d + 2) * meanN for d in pool_depths)
+    alg_bytes = sum((d + 2) * st["test_samples"][d] for d in pool_depths)
     test_ms = sum(stats_acc["test_ms"][d] for d in pool_depths) / args.steps
     achieved = alg_bytes / (test_ms / 1e3) / 1e9 if test_ms > 0 else 0.0
     try:
@@ -508,33 +546,45 @@ def main():
     for hh in hs_e2e:
         F.fbn_destroy(hh)
 
-    # the plain edge-level GPU form on the same workload, for comparison
+    # the plain edge-level GPU form (one CTA per edge, Section IV-A) on the
+    # same workload, same launch pattern (a batch: one launch per depth over
+    # every problem's edges), for comparison
     plain = None
     if not args.no_plain and args.form == "pool":
         if w["kind"] == "single":
-            hp = F.fbn_create(data_dev, w["ar"], form="plain", device=local)
-            F.fbn_set_stream(hp, stream)
-            F.fbn_learn_skeleton(hp, w["alpha"], w["max_depth"], adj_out=outs[0])
-            pm = []
-            for _ in range(max(2, min(args.steps, 5))):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                F.fbn_learn_skeleton(hp, w["alpha"], w["max_depth"], adj_out=outs[0])
-                e1.record(stream)
-                torch.cuda.synchronize()
-                pm.append(e0.elapsed_time(e1))
-            sp = F.fbn_get_stats(hp)
-            pms = sum(pm) / len(pm)
-            plain = {"value": world * sum(sp["tests_oracle"]) / (pms / 1e3), "ms_per_step": pms,
-                     "tests_executed": sum(sp["tests"])}
+            hps = [F.fbn_create(data_dev, w["ar"], form="plain", device=local)]
+        else:
+            hps = [F.fbn_create(torch.from_numpy(d).cuda(), a, form="plain", device=local) for d, a in w["probs"]]
+        F.fbn_set_stream(hps[0], stream)
+
+        def plain_step():
+            if w["kind"] == "single":
+                F.fbn_learn_skeleton(hps[0], w["alpha"], w["max_depth"], adj_out=outs[0])
+            else:
+                F.fbn_learn_skeleton_batch(hps, w["alpha"], w["max_depth"], adj_out=outs)
+        plain_step()
+        pm = []
+        for _ in range(max(2, min(args.steps, 3 if w["kind"] == "batch" else 5))):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plain_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            pm.append(e0.elapsed_time(e1))
+        sp = F.fbn_get_stats(hps[0])
+        pms = sum(pm) / len(pm)
+        plain = {"value": world * sum(sp["tests_oracle"]) / (pms / 1e3), "ms_per_step": pms,
+                 "tests_executed": sum(sp["tests"]), "steps": len(pm),
+                 "chosen_over_plain": (world * tests / (ms / 1e3)) / (world * sum(sp["tests_oracle"]) / (pms / 1e3))}
+        for hp in hps:
             F.fbn_destroy(hp)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        cpu = oracle_rate(w, st)
+        cpu = oracle_rate(w, st, args)
 
     if rank == 0:
         clk["window"] = "0.6 s untimed soak of identical steps followed by the timed steps"

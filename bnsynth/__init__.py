@@ -29,7 +29,7 @@ import math
 import numpy as np
 
 __all__ = ["Network", "random_network", "sample", "make_dataset", "WORKLOADS",
-           "workload", "batched_workload", "chain", "fork", "collider",
+           "workload", "batched_workload", "batched_size", "chain", "fork", "collider",
            "SEED_BASE", "BATCH_SEED_BASE"]
 
 SEED_BASE = 2212042590        # workload k (1-based) uses SEED_BASE + k
@@ -125,6 +125,14 @@ def workload(name: str, n_samples: int | None = None):
                                  w["arities"], w["dirichlet"],
                                  w["n_samples"] if n_samples is None else n_samples)
     return data, ar, w["alpha"], w["max_depth"], net
+
+
+def batched_size(p: int, n_range=(20, 300), samples_range=(1000, 50000)):
+    """(n, N) of problem p of the batched workload, without drawing its network or samples."""
+    rng = np.random.default_rng(BATCH_SEED_BASE + p)
+    n = int(rng.integers(n_range[0], n_range[1] + 1))
+    lo, hi = math.log(samples_range[0]), math.log(samples_range[1])
+    return n, int(round(math.exp(rng.uniform(lo, hi))))
 
 
 def batched_workload(n_problems: int = 256, first: int = 0, n_range=(20, 300),

@@ -90,6 +90,8 @@ typedef struct fbn_stats {
     double  gram_ms;                        /* device time of the one-hot Gram (0 if not used) */
     int64_t gram_rows;                      /* M = sum of arities, when the Gram ran */
     int64_t gram_samples;                   /* padded samples of the Gram */
+    int64_t test_samples[FBN_MAX_DEPTHS];   /* sum over the tests_oracle[d] tests of their data set's N
+                                               (in a batch each test counts its own problem's samples) */
 } fbn_stats;
 
 typedef struct fbn_handle fbn_handle;
@@ -223,12 +225,15 @@ void fbn_destroy(fbn_handle* h);
  * cudaFree would stall the device.  The paper has no counterpart: this is an
  * interface for such callers, not a step of the method.
  *   data     : device, uint8 [n_vars][ld] variable-major, 16-byte aligned,
- *              ld >= n_samples and a multiple of 16; values must lie below
- *              their arity (not checked here).
+ *              ld >= n_samples and a multiple of 16.  The d + 2 rows of the
+ *              test are checked on the device before counting: if a value is
+ *              >= its arity, nothing is counted, table_out is not written and
+ *              all three outputs are NaN.
  *   arities  : host, uint8 [n_vars], each >= 2.
  *   x, y, z, nz : as in fbn_ci_test (z in host memory).
  *   out      : device, 3 doubles written in stream order: G^2, df, p
- *              (p = NaN if the p-value iteration failed).
+ *              (p alone NaN: the p-value iteration failed; all three NaN: a
+ *              data value out of range).
  *   table_out: device, nullable; int32 counts in the fbn_ci_table layout.
  *   stream   : cudaStream_t (NULL = the legacy default stream).
  * The call is asynchronous and allocates nothing: it calls no cudaMalloc,
@@ -238,6 +243,8 @@ void fbn_destroy(fbn_handle* h);
  * rejected with FBN_ETOOBIG.  The first call on a device looks up that
  * array's device address (cudaGetSymbolAddress) and sets the kernel's
  * shared-memory limit, so make that first call before any stream capture.
+ * That set-up is kept per device ordinal for the life of the process and does
+ * not survive cudaDeviceReset: do not reset a device between calls.
  * All calls on a device share the one scratch array: calls that overlap on
  * the GPU (different streams, or other host threads) race and must be
  * serialised by the caller.  Errors: FBN_EINVAL, FBN_ETOOBIG, FBN_ECUDA, with

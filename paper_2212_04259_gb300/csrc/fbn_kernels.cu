@@ -678,14 +678,16 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
     if (!ctr->active) return;
     const int d = ctr->d;
     const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
-    unsigned long long my_tests = 0, my_removed = 0;
+    unsigned long long my_tests = 0, my_removed = 0, my_samples = 0;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
          k += (long long)gridDim.x * blockDim.x) {
         const long long e = k < n0 ? k : edge_cap - n1 + (k - n0);
         const EdgeWork w = edges[e];
         const unsigned long long ma = min_accept[e];
         const bool rm = ma < (unsigned long long)w.total;
-        my_tests += rm ? ma + 1 : (unsigned long long)w.total;
+        const unsigned long long t = rm ? ma + 1 : (unsigned long long)w.total;
+        my_tests += t;
+        my_samples += t * (unsigned long long)probs[w.prob].N;
         if (!rm) continue;
         my_removed += 1;
         const ProblemDev P = probs[w.prob];
@@ -716,9 +718,11 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
     for (int o = 16; o > 0; o >>= 1) {
         my_tests += __shfl_xor_sync(0xffffffffu, my_tests, o);
         my_removed += __shfl_xor_sync(0xffffffffu, my_removed, o);
+        my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
     }
     if ((threadIdx.x & 31) == 0) {
         if (my_tests) atomicAdd(&ctr->tests_oracle, my_tests);
+        if (my_samples) atomicAdd(&ctr->test_samples, my_samples);
         if (my_removed) atomicAdd(&ctr->removed, my_removed);
     }
 }
@@ -742,6 +746,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
             rec[d].edges = E;
             rec[d].tests = (long long)ctr->tests;
             rec[d].tests_oracle = (long long)ctr->tests_oracle;
+            rec[d].test_samples = (long long)ctr->test_samples;
             rec[d].removed = (long long)ctr->removed;
             rec[d].t_end = gtime();
         }
@@ -750,7 +755,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
                           next >= kMaxDepthRecords;
         for (int c = 0; c < 2; ++c)
             ctr->n_edges[c] = ctr->maxc[c] = ctr->next_item[c] = ctr->total_items[c] = ctr->max_cells[c] = 0;
-        ctr->tests = ctr->tests_oracle = ctr->removed = 0;
+        ctr->tests = ctr->tests_oracle = ctr->removed = ctr->test_samples = 0;
         ctr->gsel = 0;
         ctr->adj_ends = 0;
         ctr->nbr_claim = 0;

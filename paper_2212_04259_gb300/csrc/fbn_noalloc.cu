@@ -36,6 +36,28 @@ std::mutex g_mu;
 bool g_ready[kNoAllocMaxDevices];
 int* g_scratch[kNoAllocMaxDevices];   // device address of g_noalloc_scratch on each device
 
+// Whether some sample value of the test's rows is not below its variable's
+// arity (block-wide, every thread gets the answer).  The other entry points
+// validate data when it enters a handle; this one reads caller-owned rows
+// directly, and an out-of-range value would index past the table (in shared
+// memory or in the scratch array), so the rows are checked before counting:
+// 16 samples per 16-byte load, four byte comparisons per 32-bit word.
+__device__ bool rows_out_of_range(const TestSpec& s)
+{
+    bool bad = false;
+    const int nvec = s.N >> 4;
+    for (int k = 0; k < s.nrows; ++k) {
+        const unsigned rr = (unsigned)s.rad[k] * 0x01010101u;   // the arity in each byte
+        const uint4* row = reinterpret_cast<const uint4*>(s.rows[k]);
+        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const uint4 w = __ldg(row + v);
+            bad |= (__vcmpgeu4(w.x, rr) | __vcmpgeu4(w.y, rr) | __vcmpgeu4(w.z, rr) | __vcmpgeu4(w.w, rr)) != 0u;
+        }
+        for (int t = (nvec << 4) + threadIdx.x; t < s.N; t += blockDim.x) bad |= s.rows[k][t] >= s.rad[k];
+    }
+    return __syncthreads_or(bad) != 0;
+}
+
 __global__ void __launch_bounds__(kTestThreads) k_ci_noalloc(TestSpec spec, int* scratch, double* out,
                                                              int32_t* table_out, int smem_ints)
 {
@@ -48,6 +70,10 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_noalloc(TestSpec spec, int*
         *status = 0;   // the previous call's status must not leak into this one
     }
     __syncthreads();
+    if (rows_out_of_range(s)) {   // a value >= its arity: no table, every output NaN
+        if (threadIdx.x == 0) out[0] = out[1] = out[2] = nan("");
+        return;
+    }
     int* M = nullptr;
     const int* T = grp_table<kTestThreads>(s, smem, smem_ints, scratch, kNoAllocTableInts, &M);
     if (!T) {   // not reached: the host admits only tables that fit the scratch

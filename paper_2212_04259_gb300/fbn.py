@@ -51,7 +51,8 @@ class Stats(C.Structure):
                 ("edges", C.c_int64 * MAX_DEPTHS), ("tests", C.c_int64 * MAX_DEPTHS),
                 ("tests_oracle", C.c_int64 * MAX_DEPTHS), ("removed", C.c_int64 * MAX_DEPTHS),
                 ("ms", C.c_double * MAX_DEPTHS), ("test_ms", C.c_double * MAX_DEPTHS),
-                ("gram_ms", C.c_double), ("gram_rows", C.c_int64), ("gram_samples", C.c_int64)]
+                ("gram_ms", C.c_double), ("gram_rows", C.c_int64), ("gram_samples", C.c_int64),
+                ("test_samples", C.c_int64 * MAX_DEPTHS)]
 
 
 _lock = threading.Lock()
@@ -247,6 +248,11 @@ def fbn_get_sepset(h: Handle, i: int, j: int):
         return None
     if k < -1:
         _check(k, h)
+    if k > len(buf):   # the call reports the full size; read again with room for it
+        buf = np.zeros(k, dtype=np.int32)
+        k = lib().fbn_get_sepset(h.ptr, i, j, _ptr(buf), len(buf))
+        if k < 0:
+            _check(k, h)
     return tuple(int(v) for v in buf[:k])
 
 
@@ -281,7 +287,8 @@ def fbn_get_stats(h: Handle) -> dict:
     return {"depths": d, "launches": int(s.launches), "edges": list(s.edges[:d]),
             "tests": list(s.tests[:d]), "tests_oracle": list(s.tests_oracle[:d]),
             "removed": list(s.removed[:d]), "ms": list(s.ms[:d]), "test_ms": list(s.test_ms[:d]),
-            "gram_ms": float(s.gram_ms), "gram_rows": int(s.gram_rows), "gram_samples": int(s.gram_samples)}
+            "gram_ms": float(s.gram_ms), "gram_rows": int(s.gram_rows), "gram_samples": int(s.gram_samples),
+            "test_samples": list(s.test_samples[:d])}
 
 
 def fbn_last_error(h: Handle | None = None) -> str:
@@ -303,8 +310,25 @@ def fbn_ci_test_noalloc(data_dev, ld: int, n_samples: int, arities, x: int, y: i
     float64 tensor of 3 (G^2, df, p), written in stream order; table_dev:
     optional device int32 tensor for the counts.  stream: torch.cuda.Stream,
     raw handle or None (the legacy default stream)."""
+    import torch
     ar = np.ascontiguousarray(arities, dtype=np.uint8)
     za = _zarr(z)
+    n_vars = len(ar)
+    dev = torch.cuda.current_device()
+
+    def need(t, name, dtype, numel):
+        # the C entry point reads and writes these buffers without knowing their sizes
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.device.index != dev:
+            raise ValueError(f"{name} must be a tensor on the current CUDA device (cuda:{dev})")
+        if t.dtype != dtype or not t.is_contiguous() or t.numel() < numel:
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of at least {numel} elements")
+
+    need(data_dev, "data_dev", torch.uint8, n_vars * int(ld))
+    need(out_dev, "out_dev", torch.float64, 3)
+    if table_dev is not None:
+        cells = int(ar[x]) * int(ar[y]) * int(np.prod([int(ar[v]) for v in za], dtype=np.int64)) \
+            if all(0 <= v < n_vars for v in list(za) + [x, y]) else 0
+        need(table_dev, "table_dev", torch.int32, cells)
     raw = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
     rc = lib().fbn_ci_test_noalloc(_ptr(data_dev), int(ld), len(ar), int(n_samples), _ptr(ar), x, y,
                                    _ptr(za) if len(za) else None, len(za), _ptr(out_dev),
