@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batched")
+    ap.add_argument("--problems", type=int, default=256, help="problems of the batched workload (the first K)")
     ap.add_argument("--form", choices=["pool", "plain"], default="pool")
     ap.add_argument("--gs", type=int, default=0)
     ap.add_argument("--group-threads", type=int, default=0, help="pin the threads per CI test (32-256)")
@@ -81,6 +82,9 @@ def parse():
                     help="depth-1 counting: tensor-core neighbourhood product or work pool")
     ap.add_argument("--statistic", choices=["g2", "x2"], default="g2", help="CI statistic (G^2 or Pearson X^2)")
     ap.add_argument("--df", choices=["fixed", "adjusted"], default="fixed", help="degrees of freedom of each test")
+    ap.add_argument("--count", choices=["auto", "hist", "bits"], default="auto",
+                    help="table counting: bit planes for small tables (auto), byte histograms only, bit planes "
+                         "wherever they fit")
     ap.add_argument("--ablation", action="store_true",
                     help="instead of the bench line: the group-size, granularity, sample-size and network-size "
                          "studies, one JSON line per configuration")
@@ -92,10 +96,10 @@ def parse():
     return ap.parse_args()
 
 
-def load_workload(name):
+def load_workload(name, problems=256):
     import bnsynth
     if name == "batched":
-        probs = bnsynth.batched_workload(256)
+        probs = bnsynth.batched_workload(problems)
         return {"kind": "batch", "probs": [(d, a) for d, a, _ in probs], "alpha": 0.05, "max_depth": -1}
     data, ar, alpha, md, _ = bnsynth.workload(name)
     return {"kind": "single", "data": data, "ar": ar, "alpha": alpha, "max_depth": md}
@@ -108,6 +112,7 @@ def workload_config(name, w, args):
         cfg.update(statistic=args.statistic, df=args.df, loop=args.loop)
     if args.loop != "device":
         cfg.update(loop=args.loop)
+    cfg.update(count=args.count)
     if w["kind"] == "single":
         n, N = w["data"].shape
         cfg.update(n_vars=n, n_samples=N, alpha=w["alpha"], max_depth=w["max_depth"],
@@ -376,7 +381,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     name = args.workload
-    w = load_workload(name)
+    w = load_workload(name, args.problems)
     if args.impl == "reference":
         return run_reference(args, w, name, rank, world)
 
@@ -401,13 +406,13 @@ def main():
         data_dev = torch.from_numpy(w["data"]).cuda()
         handles = [F.fbn_create(data_dev, w["ar"], form=args.form, group_size=gs, device=local,
                                 group_threads=args.group_threads, depth1=args.depth1, statistic=args.statistic,
-                                df=args.df, loop=args.loop)]
+                                df=args.df, loop=args.loop, count=args.count)]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((w["data"].shape[0],) * 2, dtype=torch.uint8, device="cuda")]
     else:
         handles = [F.fbn_create(torch.from_numpy(d).cuda(), a, form=args.form, group_size=gs, device=local,
                                 group_threads=args.group_threads, depth1=args.depth1, statistic=args.statistic,
-                                df=args.df, loop=args.loop)
+                                df=args.df, loop=args.loop, count=args.count)
                    for d, a in w["probs"]]
         F.fbn_set_stream(handles[0], stream)
         outs = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8, device="cuda") for d, _ in w["probs"]]
@@ -509,14 +514,14 @@ def main():
         n = w["data"].shape[0]
         adj_host = torch.zeros((n, n), dtype=torch.uint8).pin_memory()
         he = F.fbn_create(host, w["ar"], form=args.form, group_size=gs, device=local, depth1=args.depth1,
-                          statistic=args.statistic, df=args.df, loop=args.loop)
+                          statistic=args.statistic, df=args.df, loop=args.loop, count=args.count)
         F.fbn_set_stream(he, stream)
         hs_e2e, hosts, adjs_host = [he], [host], [adj_host]
     else:
         hosts = [torch.from_numpy(d).pin_memory() for d, _ in w["probs"]]
         adjs_host = [torch.zeros((d.shape[0],) * 2, dtype=torch.uint8).pin_memory() for d, _ in w["probs"]]
         hs_e2e = [F.fbn_create(hh, a, form=args.form, group_size=gs, device=local, depth1=args.depth1,
-                               statistic=args.statistic, df=args.df, loop=args.loop)
+                               statistic=args.statistic, df=args.df, loop=args.loop, count=args.count)
                   for hh, (_, a) in zip(hosts, w["probs"])]
         F.fbn_set_stream(hs_e2e[0], stream)
     e2e_ms, d2h = [], 0

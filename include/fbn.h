@@ -53,6 +53,11 @@ extern "C" {
 #define FBN_DF_ADJUSTED 1  /* df = sum over strata with N_++z > 0 of (values of X seen - 1)(values of Y seen - 1);
                               a test with df = 0 cannot reject (p = 1) */
 
+#define FBN_COUNT_AUTO 0   /* tables of small tests (every arity <= 4, at most 2 conditioning variables, few
+                              cells) counted from bit planes with popcounts, the others by byte histograms */
+#define FBN_COUNT_HIST 1   /* every table by the byte histogram (shared-memory reductions, or a global table) */
+#define FBN_COUNT_BITS 2   /* bit planes for every test that qualifies and fits shared memory, whatever its size */
+
 #define FBN_LOOP_DEVICE 0  /* the depths after any launched directly run as one CUDA graph whose while node the
                               device drives (no host round trip between depths) */
 #define FBN_LOOP_HOST   1  /* the same kernels, one depth at a time from the host, which reads the loop flag
@@ -72,7 +77,9 @@ typedef struct fbn_options {
     int32_t statistic;   /* FBN_STAT_G2 (default) or FBN_STAT_X2: the statistic of every CI test */
     int32_t df_mode;     /* FBN_DF_FIXED (default) or FBN_DF_ADJUSTED: degrees of freedom of every CI test */
     int32_t loop;        /* FBN_LOOP_DEVICE (default) or FBN_LOOP_HOST: who drives the depth loop */
-    int32_t reserved[6]; /* must be zero */
+    int32_t count;       /* FBN_COUNT_*: how contingency tables are counted (pool form and explicit tests; the
+                            plain form always uses byte histograms) */
+    int32_t reserved[5]; /* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */

@@ -36,7 +36,8 @@ def _deps_mtime() -> float:
 
 
 def _compile(src: str, obj: str, extra) -> None:
-    cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj + ".tmp"]
+    # FBN_NVCC_FLAGS: extra nvcc flags (space separated), e.g. -D settings of the kernels
+    cmd = [nvcc(), *ARCH, *FLAGS, *os.environ.get("FBN_NVCC_FLAGS", "").split(), *extra, "-c", src, "-o", obj + ".tmp"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

@@ -27,8 +27,11 @@ thread_local std::string g_create_error;
 constexpr size_t kSmemBytes = 100 * 1024;     // dynamic shared memory of a CTA test group: 2 CTAs / SM with the ~9 KB static
 constexpr long long kSplitStride = 4096;        // cells of a split test's global table at most
 constexpr size_t kWarpSmemBytes = 56 * 1024;  // dynamic shared memory of a CTA of 8 warp groups (3 CTAs / SM)
+constexpr size_t kBitsSmemBytes = 36 * 1024;  // the bit-plane pool: 8 groups of 32 x 32 counter words, table and
+                                              // marginals (4 CTAs / SM)
 constexpr int kCritCap = 8192;                // critical-value cache slots (power of two)
 constexpr int kCritDense = 8192;              // critical values kept in a dense table: df < kCritDense
+constexpr int kBitsCellsAuto = 64;            // largest table counted from bit planes by default
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count)
@@ -53,6 +56,30 @@ __global__ void k_validate(const uint8_t* data, int64_t ld, int n, int64_t N, co
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
         if (row[s] >= r) atomicMin(first_bad, (unsigned long long)v * (unsigned long long)N + s);
+    }
+}
+
+// Bit planes of the samples: word w of plane b of variable v holds bit b of
+// the values of samples 32 w .. 32 w + 31.  One thread per word reads its 32
+// bytes (two 16-byte loads; the zero padding of the rows covers the words
+// past the samples, which therefore stay zero).
+__global__ void k_planes(const uint8_t* __restrict__ data, int64_t ld, int64_t wp, uint32_t* __restrict__ planes)
+{
+    const int v = blockIdx.y;
+    const uint8_t* row = data + (long long)v * ld;
+    for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < wp; w += (long long)gridDim.x * blockDim.x) {
+        const uint4* p = reinterpret_cast<const uint4*>(row + w * 32);
+        const uint4 a = p[0], b = p[1];
+        const unsigned q[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        unsigned m0 = 0, m1 = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const unsigned val = (q[k >> 2] >> ((k & 3) * 8)) & 0xFFu;
+            m0 |= (val & 1u) << k;
+            m1 |= ((val >> 1) & 1u) << k;
+        }
+        planes[(2LL * v) * wp + w] = m0;
+        planes[(2LL * v + 1) * wp + w] = m1;
     }
 }
 
@@ -95,6 +122,7 @@ struct Workspace {
     long long* crit_keys = nullptr;
     double* crit_vals = nullptr;
     double* crit_dense = nullptr;
+    float2* crit_dense_f = nullptr;
     double crit_alpha = -1.0;
     cudaEvent_t kev[2 * FBN_MAX_DEPTHS + 2] = {};   // the Gram's window at the end
     DepthRecord* d_rec = nullptr;
@@ -118,7 +146,7 @@ struct Workspace {
     unsigned* split_ticket = nullptr;
     bool split_dirty = false;
     // launch geometry of the device, fixed once (kernel attributes set)
-    int dev_sms = 0, grid_small = 0, grid_big = 0;
+    int dev_sms = 0, grid_small = 0, grid_big = 0, grid_bits = 0;
     // the problem descriptors and vertex maps as last uploaded (skipped when
     // unchanged), staged through pinned memory
     std::vector<uint8_t> up_last;
@@ -148,6 +176,7 @@ struct Workspace {
         if (h_ctr) cudaFreeHost(h_ctr);
         dfree(binom); dfree(vtx_prob); dfree(vtx_first); dfree(probs);
         dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals); dfree(crit_dense);
+        dfree(crit_dense_f);
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
         dfree(split_tab); dfree(split_ticket);
         if (events) {
@@ -189,6 +218,8 @@ struct fbn_handle {
     int max_arity = 0;
     std::vector<uint8_t> h_ar;
     uint8_t* d_data = nullptr;
+    uint32_t* d_planes = nullptr;       // two bit planes per variable (see k_planes)
+    int64_t plane_ld = 0;               // words per plane, a multiple of 4
     uint8_t* d_ar = nullptr;
     uint8_t* d_adj = nullptr;
     int32_t* d_nbr = nullptr;
@@ -273,6 +304,7 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         CK(dalloc(&ws.crit_keys, kCritCap));
         CK(dalloc(&ws.crit_vals, kCritCap));
         CK(dalloc(&ws.crit_dense, kCritDense));
+        CK(dalloc(&ws.crit_dense_f, kCritDense));
         CK(dalloc(&ws.split_tab, kSplitItems * kSplitStride));
         CK(dalloc(&ws.split_ticket, kSplitItems));
         ws.split_dirty = true;
@@ -384,6 +416,30 @@ int check_status(fbn_handle* h, unsigned status)
     if (status & kStatusEdges) return fail(h, FBN_ECUDA, "edge list overflow");
     if (status & kStatusTimeout) return fail(h, FBN_ETIMEOUT, "a bounded device wait gave up");
     if (status & kStatusScratch) return fail(h, FBN_ENOMEM, "global table scratch too small");
+    return FBN_OK;
+}
+
+// Largest table a test of h counts from the bit planes (0: none): the
+// option's choice; the plain edge-level form keeps the byte histogram.
+int bits_cells(const fbn_handle* h)
+{
+    if (h->opt.form == FBN_FORM_PLAIN || h->opt.count == FBN_COUNT_HIST) return 0;
+    return h->opt.count == FBN_COUNT_BITS ? (int)kMaxCells : kBitsCellsAuto;
+}
+
+// Whether the explicit test of (x, y | z) is counted from the bit planes.
+bool test_uses_bits(const fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, long long cells)
+{
+    int mx = std::max(h->h_ar[x], h->h_ar[y]);
+    for (int k = 0; k < nz; ++k) mx = std::max<int>(mx, h->h_ar[z[k]]);
+    return bits_shape_ok(nz, mx, h->N) && cells <= bits_cells(h);
+}
+
+int launch_planes(fbn_handle* h, cudaStream_t st)
+{
+    dim3 grid((unsigned)std::min<long long>((h->plane_ld + 255) / 256, 64), h->n);
+    k_planes<<<grid, 256, 0, st>>>(h->d_data, h->ld, h->plane_ld, h->d_planes);
+    CK(cudaGetLastError());
     return FBN_OK;
 }
 
@@ -695,6 +751,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         d.data = q->d_data; d.ar = q->d_ar; d.adj = q->d_adj; d.nbr = q->d_nbr; d.eid = q->d_eid; d.npos = q->d_npos; d.deg = q->d_deg;
         d.sep_len = q->d_sep_len; d.sep_off = q->d_sep_off; d.ld = q->ld; d.n = q->n; d.N = (int32_t)q->N;
         d.max_arity = q->max_arity; d.pad = 0;
+        d.planes = q->d_planes; d.plane_ld = q->plane_ld;
     }
     int rc = grow_workspace(h, ws, edge_cap, max_n, k, total_vtx);
     if (rc) return rc;
@@ -754,9 +811,10 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         // CTAs of the small-table pool (any group size) and of the big-table pool
         ws.grid_small = sms * std::max(1, pool_blocks_per_sm(kClassWarp, kWarpSmemBytes));
         ws.grid_big = sms * std::max(1, pool_blocks_per_sm(kClassCta, kSmemBytes));
+        ws.grid_bits = sms * std::max(1, pool_blocks_per_sm(kClassBits, kBitsSmemBytes));
         ws.dev_sms = sms;
     }
-    const int dev_sms = ws.dev_sms, grid_small = ws.grid_small, grid_big = ws.grid_big;
+    const int dev_sms = ws.dev_sms, grid_small = ws.grid_small, grid_big = ws.grid_big, grid_bits = ws.grid_bits;
     const long long groups[4] = {(long long)grid_small * 8, (long long)grid_small * 4, (long long)grid_small * 2,
                                  (long long)grid_small};
     const long long groups_big[4] = {(long long)grid_big * 8, (long long)grid_big * 4, (long long)grid_big * 2,
@@ -772,15 +830,17 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     if (ws.crit_alpha != alpha) {
         CK(cudaMemsetAsync(ws.crit_keys, 0, kCritCap * sizeof(long long), st));
         CK(cudaMemsetAsync(ws.crit_dense, 0, kCritDense * sizeof(double), st));
+        CK(cudaMemsetAsync(ws.crit_dense_f, 0, kCritDense * sizeof(float2), st));
         ws.crit_alpha = alpha;
     }
-    CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, kCritDense, ws.crit_dense};
+    CritTableDev ct{ws.crit_keys, ws.crit_vals, kCritCap, kCritDense, ws.crit_dense, ws.crit_dense_f};
 
     CK(cudaMemsetAsync(ws.d_rec, 0, kMaxDepthRecords * sizeof(DepthRecord), st));
     CK(cudaMemsetAsync(ws.hist, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(ws.cursor, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
     DepthCounters c0{};
     c0.active = 1;
+    c0.bits_ok = 1;
     c0.rec = ws.d_rec;
     *ws.h_ctr = c0;
     CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
@@ -801,6 +861,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     base.split_tab = ws.split_tab;
     base.split_ticket = ws.split_ticket;
     base.split_stride = kSplitStride;
+
     if (ws.split_dirty) {
         CK(cudaMemsetAsync(ws.split_tab, 0, kSplitItems * kSplitStride * sizeof(int), st));
         CK(cudaMemsetAsync(ws.split_ticket, 0, kSplitItems * sizeof(unsigned), st));
@@ -817,8 +878,12 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
                 sc[cls].hist = ws.hist + cls * ws.ord_cap;
                 sc[cls].alive = ws.alive + cls * ws.ord_cap;
                 sc[cls].base = ws.base + cls * ws.ord_cap;
-                for (int k = 0; k < 4; ++k) sc[cls].groups[k] = cls == 0 ? groups[k] : groups_big[k];
+                for (int k = 0; k < 4; ++k) {
+                    sc[cls].groups[k] = cls == 0 ? groups[k] : groups_big[k];
+                    sc[cls].groups_bits[k] = ((long long)grid_bits * 8) >> k;
+                }
                 sc[cls].smem_ints = (long long)((cls == 0 ? kWarpSmemBytes : kSmemBytes) / 4);
+                sc[cls].smem_ints_bits = (long long)(kBitsSmemBytes / 4);
             }
             launch_order(ws.edges, ws.edge_cap, nclass, ws.d_ctr, sc, ws.cursor, ws.cursor + ws.ord_cap, ws.sorted,
                          mean_n, forced, kSplitStride, 1, grid_aux, st);
@@ -839,20 +904,25 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             }
             a.base = ws.base + cls * ws.ord_cap;
             a.sorted = ws.sorted;
+            if (small) {   // the bit-plane pool first; exactly one of the two runs the class
+                PoolArgs b = a;
+                b.smem_ints = (int)(kBitsSmemBytes / 4);
+                launch_pool_bits(b, grid_bits, kBitsSmemBytes, st);
+            }
             launch_pool(a, cls, small ? grid_small : grid_big, smem, st);
         }
     };
     auto enqueue_head = [&]() {
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
         launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, gs_forced, gs_edges, ws.binom, ws.brows, wcap,
-                     ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
+                     bits_cells(h), ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
     };
     auto enqueue_tail = [&]() {
         launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
                      grid_aux, st);
         launch_depth_end(ws.d_ctr, ws.d_rec, max_depth, ws.hist, ws.cursor, st);
     };
-    const int body_launches = plain ? 7 : 9;
+    const int body_launches = plain ? 7 : 10;
     auto capture_loop = [&]() -> cudaError_t {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaGraphCreate(&g, 0);
@@ -925,11 +995,12 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         };
         const void* ptrs[] = {ws.probs, ws.vtx_prob, ws.vtx_first, ws.binom, ws.edges, ws.min_accept, ws.d_ctr,
                               ws.hist, ws.alive, ws.base, ws.cursor, ws.sorted, ws.gscratch, ws.sep_pool, ws.d_rec,
-                              ws.crit_keys, ws.crit_vals, ws.crit_dense, ws.split_tab, ws.split_ticket};
+                              ws.crit_keys, ws.crit_vals, ws.crit_dense, ws.crit_dense_f, ws.split_tab,
+                              ws.split_ticket};
         put(ptrs, sizeof ptrs);
         const long long ints[] = {total_vtx, gs_forced, gs_edges, ws.brows, wcap, ws.edge_cap, ws.ord_cap, forced,
-                                  grid_aux, grid_small, grid_big, ws.gs_cells, ws.sep_cap, max_depth, plain,
-                                  h->opt.statistic, h->opt.df_mode,
+                                  grid_aux, grid_small, grid_big, grid_bits, ws.gs_cells, ws.sep_cap, max_depth, plain,
+                                  h->opt.statistic, h->opt.df_mode, bits_cells(h),
                                   groups[0], groups[1], groups[2], groups[3]};
         put(ints, sizeof ints);
         put(&mean_n, sizeof mean_n);
@@ -1150,7 +1221,7 @@ int run_ci(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, lo
     CK(cudaMemsetAsync(h->d_status, 0, sizeof(unsigned), st));
     launch_ci_tests(h->d_prob, h->d_ci, 1, h->d_ci_out, want_table ? h->d_table : nullptr,
                     gints ? h->d_gscratch : nullptr, gints, h->d_status, kSmemBytes, h->opt.statistic, h->opt.df_mode,
-                    st);
+                    test_uses_bits(h, x, y, z, nz, cells), st);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_ci_out, h->d_ci_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -1165,7 +1236,7 @@ void free_handle(fbn_handle* h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     set_snapshot(h, nullptr);
     h->ws.release();
-    dfree(h->d_data); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
+    dfree(h->d_data); dfree(h->d_planes); dfree(h->d_ar); dfree(h->d_adj); dfree(h->d_nbr); dfree(h->d_eid); dfree(h->d_npos); dfree(h->d_deg);
     dfree(h->d_sep_len); dfree(h->d_sep_off); dfree(h->d_prob);
     dfree(h->d_sep_cnt);
     dfree(h->d_ci); dfree(h->d_ci_out); dfree(h->d_status); dfree(h->d_table); dfree(h->d_gscratch);
@@ -1201,7 +1272,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 6; ++k)
+        for (int k = 0; k < 5; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
         if (o.loop != FBN_LOOP_DEVICE && o.loop != FBN_LOOP_HOST) return fail(nullptr, FBN_EINVAL, "bad loop %d", o.loop);
         if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
@@ -1216,6 +1287,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
             return fail(nullptr, FBN_EINVAL, "bad statistic %d", o.statistic);
         if (o.df_mode != FBN_DF_FIXED && o.df_mode != FBN_DF_ADJUSTED)
             return fail(nullptr, FBN_EINVAL, "bad df_mode %d", o.df_mode);
+        if (o.count < FBN_COUNT_AUTO || o.count > FBN_COUNT_BITS) return fail(nullptr, FBN_EINVAL, "bad count %d", o.count);
         if (o.depth1 == FBN_DEPTH1_TENSOR && (o.statistic != FBN_STAT_G2 || o.df_mode != FBN_DF_FIXED))
             return fail(nullptr, FBN_EINVAL, "depth1 tensor takes the G^2 statistic with fixed df only");
     }
@@ -1265,6 +1337,8 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     h->stream = h->own_stream;
     const size_t nn = (size_t)n_vars * n_vars;
     CKC(dalloc(&h->d_data, (size_t)n_vars * h->ld));
+    h->plane_ld = ((n_samples + 31) / 32 + 3) / 4 * 4;   // 32-sample words, whole uint4 groups
+    CKC(dalloc(&h->d_planes, (size_t)n_vars * 2 * h->plane_ld));
     CKC(dalloc(&h->d_ar, n_vars));
     CKC(dalloc(&h->d_adj, nn));
     CKC(dalloc(&h->d_nbr, nn));
@@ -1293,6 +1367,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         k_validate<<<grid, 256, 0, st>>>(h->d_data, h->ld, n_vars, n_samples, h->d_ar, bad);
     }
     CKC(cudaGetLastError());
+    if (launch_planes(h, st)) return bail(FBN_ECUDA);
     unsigned long long first_bad = 0;
     CKC(cudaMemcpyAsync(h->h_status, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
@@ -1320,6 +1395,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     P.data = h->d_data; P.ar = h->d_ar; P.adj = h->d_adj; P.nbr = h->d_nbr; P.eid = h->d_eid; P.npos = h->d_npos; P.deg = h->d_deg;
     P.sep_len = h->d_sep_len; P.sep_off = h->d_sep_off; P.ld = h->ld; P.n = n_vars; P.N = (int32_t)n_samples;
     P.max_arity = max_ar;
+    P.planes = h->d_planes; P.plane_ld = h->plane_ld;
     CKC(cudaMemcpyAsync(h->d_prob, &P, sizeof P, cudaMemcpyHostToDevice, st));
     CKC(cudaStreamSynchronize(st));
 #undef CKC
@@ -1341,6 +1417,8 @@ int fbn_update_data(fbn_handle* h, const uint8_t* data)
     dim3 grid((unsigned)std::min<long long>((h->N + 255) / 256, 64), h->n);
     k_validate<<<grid, 256, 0, st>>>(h->d_data, h->ld, h->n, h->N, h->d_ar, bad);
     CK(cudaGetLastError());
+    const int prc = launch_planes(h, st);
+    if (prc) return prc;
     CK(cudaMemcpyAsync(h->h_status, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     unsigned long long first_bad;

@@ -125,7 +125,10 @@ __device__ __forceinline__ double crit_get(const CritTable& t, long long df, dou
         if (v > 0.0) return v;
         bool capped = false;
         const double c = chisq_crit((double)df, alpha, status, &capped);
-        if (!capped) t.dense[df] = c;
+        if (!capped) {
+            t.dense[df] = c;
+            if (t.dense_f) t.dense_f[df] = make_float2(__double2float_rd(c), __double2float_ru(c));
+        }
         return c;
     }
     unsigned h = (unsigned)(df * 0x9E3779B97F4A7C15ULL >> 40) & (unsigned)(t.cap - 1);
@@ -194,6 +197,10 @@ struct TestSpec {
     int rx, ry;
     int N;
     long long cells;  // product of all radices
+    // bit planes of the first kBitsMaxD + 2 rows, at the test's first sample
+    // (plane 0; plane 1 pstride uint4 further), or nullptr without planes
+    const uint4* prow[kBitsMaxD + 2];
+    long long pstride;
 };
 
 template <int G>
@@ -258,7 +265,7 @@ __device__ __forceinline__ void grp_sum2(double& a, double& b, double* red)
     }
 }
 
-enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3, kLane16 = 4 };
+enum CountMode { kLane = 0, kWarp = 1, kShared = 2, kGlobal = 3, kLane16 = 4, kBits = 5 };
 
 template <int MODE>
 __device__ __forceinline__ void bump(int* base, unsigned idx)
@@ -515,6 +522,114 @@ __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
     }
 }
 
+// --------------------------------------------------------------------------
+// Counting from bit planes (every variable of the test has arity <= 4 and at
+// most one conditioning variable: C = r_z r_x r_y <= 64 cells).  With the
+// values' two bits held as 32-sample words per variable (plane 0: bit 0,
+// plane 1: bit 1), the samples of a word that fall in cell (z, x, y) are the
+// AND of one minterm of the planes per variable, and their count is one POPC
+// of that AND: one LOP3 and one POPC per cell and 32 samples, where the byte
+// histogram spends one shared-memory reduction per sample.
+//
+// A thread takes one 32-sample word of every plane at a time -- the next
+// word's planes are loaded while the current one is counted -- and keeps the
+// 64 cells of the fixed [z][x][y] = [4][4][4] layout as 16-bit counters packed
+// two to a register (32 registers, indices known at compile time), so the
+// sample loop touches no shared memory.  The strata and x loops stop at the
+// test's arities; the y loop always runs its 4 values (a value the variable
+// cannot take pops zero), which keeps the innermost loop free of branches.
+// The one partial word at the end of the samples is peeled off with its
+// validity mask.  A counter grows by at most 32 per word and a thread sees at
+// most ceil(N / 32 / G) words: below 2^16 while N <= kBitsMaxN.
+constexpr int kBitsWords = 32;   // counter words per thread: 4 strata x 4 x 2
+
+__device__ __forceinline__ unsigned minterm1(unsigned m, unsigned p0, unsigned p1, int a)
+{
+    // m & [value == a] from the value's bit planes; a is a compile-time
+    // constant wherever this is called from an unrolled loop (one LOP3)
+    return m & ((a & 1) ? p0 : ~p0) & ((a & 2) ? p1 : ~p1);
+}
+
+// Counter word of cell (z, x, y) (the fold uses the same layout).
+__host__ __device__ __forceinline__ int bits_word_of(int z, int x, int y)
+{
+    return z * 8 + x * 2 + (y >> 1);
+}
+
+struct BitsWord {
+    unsigned x0, x1, y0, y1, z0, z1;
+};
+
+__device__ __forceinline__ BitsWord bits_load(const unsigned* __restrict__ xr, const unsigned* __restrict__ yr,
+                                              const unsigned* __restrict__ zr, int ps, int w, int d)
+{
+    BitsWord b;
+    b.x0 = __ldg(xr + w);
+    b.x1 = __ldg(xr + ps + w);
+    b.y0 = __ldg(yr + w);
+    b.y1 = __ldg(yr + ps + w);
+    b.z0 = d ? __ldg(zr + w) : 0u;
+    b.z1 = d ? __ldg(zr + ps + w) : 0u;
+    return b;
+}
+
+__device__ __forceinline__ void bits_count(unsigned* acc, const BitsWord& b, unsigned valid, int d, int rz, int rx)
+{
+#pragma unroll
+    for (int c = 0; c < kBitsMaxArity; ++c) {
+        if (c >= rz) break;
+        const unsigned zm = d ? minterm1(valid, b.z0, b.z1, c) : valid;
+#pragma unroll
+        for (int a = 0; a < kBitsMaxArity; ++a) {
+            if (a >= rx) break;
+            const unsigned xa = minterm1(zm, b.x0, b.x1, a);
+            const unsigned n0 = (unsigned)__popc(minterm1(xa, b.y0, b.y1, 0));
+            const unsigned n1 = (unsigned)__popc(minterm1(xa, b.y0, b.y1, 1));
+            const unsigned n2 = (unsigned)__popc(minterm1(xa, b.y0, b.y1, 2));
+            const unsigned n3 = (unsigned)__popc(minterm1(xa, b.y0, b.y1, 3));
+            acc[c * 8 + a * 2] += n0 + (n1 << 16);
+            acc[c * 8 + a * 2 + 1] += n2 + (n3 << 16);
+        }
+    }
+}
+
+// cnt: this thread's column of kBitsWords counter words with stride G
+// (bits_word_of layout).  Not inlined: one call per test, and the sample loop
+// gets the kernel's whole register budget.
+template <int G>
+__device__ __noinline__ void count_bits(const TestSpec& s, int* cnt)
+{
+    const int rx = s.rx, d = s.nrows - 2;
+    const int rz = d ? s.rad[0] : 1;
+    const int nw = (s.N + 31) >> 5;
+    const int full = s.N >> 5;             // words with every sample below N
+    const int ps = (int)(4 * s.pstride);   // words per plane (< 2^26 for N <= kBitsMaxN)
+    const unsigned* __restrict__ xr = reinterpret_cast<const unsigned*>(s.prow[d]);
+    const unsigned* __restrict__ yr = reinterpret_cast<const unsigned*>(s.prow[d + 1]);
+    const unsigned* __restrict__ zr = reinterpret_cast<const unsigned*>(s.prow[0]);
+    unsigned acc[kBitsWords];
+#pragma unroll
+    for (int k = 0; k < kBitsWords; ++k) acc[k] = 0u;
+    int w = Grp<G>::rank();
+    if (w < full) {
+        BitsWord cur = bits_load(xr, yr, zr, ps, w, d);
+        for (;;) {
+            const int wn = w + G;
+            const bool more = wn < full;
+            BitsWord nxt = cur;
+            if (more) nxt = bits_load(xr, yr, zr, ps, wn, d);   // in flight while cur is counted
+            bits_count(acc, cur, ~0u, d, rz, rx);
+            w = wn;
+            if (!more) break;
+            cur = nxt;
+        }
+    }
+    if (w == full && full < nw) bits_count(acc, bits_load(xr, yr, zr, ps, w, d), (1u << (s.N & 31)) - 1u, d, rz, rx);
+#pragma unroll
+    for (int k = 0; k < kBitsWords; ++k)
+        if ((k >> 3) < rz) cnt[k * G] = (int)acc[k];
+}
+
 // Shared-memory ints needed by each counting strategy for a table of C cells
 // (marg = marginal entries); kGlobal when none fits.  kLane16 (warp groups)
 // packs two lane-private counters per word: a lane counts at most
@@ -537,33 +652,53 @@ __device__ __forceinline__ int pick_mode(long long C, long long marg, long long 
 
 // Count the table of the test and merge private copies.  Returns the merged
 // table T and sets *M to the space for the marginals; returns nullptr when the
-// table fits neither the slice nor the global scratch.
-template <int G>
+// table fits neither the slice nor the global scratch.  bits_cells: largest
+// table counted from the bit planes when the test qualifies (0: never).
+template <int G, bool BITS = false>
 __device__ int* grp_table(const TestSpec& s, int* slice, long long slice_ints, int* gtab, long long gtab_ints,
                           int** M)
 {
     const long long C = s.cells;
     const long long nz = C / (s.rx * s.ry);
     const long long marg = nz * (s.rx + s.ry + 1);
-    const int mode = pick_mode<G>(C, marg, slice_ints, s.N);
+    // BITS: the caller admits only tests that bits_shape_ok accepts, whose
+    // kBitsWords * G counter words, table and marginals fit the slice
+    const int mode = BITS ? kBits : pick_mode<G>(C, marg, slice_ints, s.N);
     if (mode == kGlobal && (gtab == nullptr || C + marg > gtab_ints)) return nullptr;
     const int r = Grp<G>::rank();
     const int lane = threadIdx.x & 31;
     const int warp = r >> 5;                     // warp within the group
     constexpr int W = Grp<G>::kWarps;
     int* cnt = mode == kGlobal ? gtab : slice;
-    const long long zero_n = mode == kLane ? C * G : mode == kLane16 ? (C + 1) / 2 * 32 : mode == kWarp ? C * W : C;
+    const long long zero_n = BITS ? 0 : mode == kLane ? C * G : mode == kLane16 ? (C + 1) / 2 * 32
+                                    : mode == kWarp ? C * W : C;
     for (int k = r; k < (int)zero_n; k += G) cnt[k] = 0;   // zero_n <= 2^27
     Grp<G>::sync();
     switch (mode) {
         case kLane: count_dispatch<G, kLane>(s, cnt + (long long)warp * C * 32 + lane); break;
         case kLane16: count_dispatch<G, kLane16>(s, cnt + lane); break;
+        case kBits:
+            if (BITS) count_bits<G>(s, cnt + r);   // writes every counter word the fold reads
+            break;
         case kWarp: count_dispatch<G, kWarp>(s, cnt + (long long)warp * C); break;
         default: count_dispatch<G, kShared>(s, cnt); break;
     }
     Grp<G>::sync();
     int* T;
-    if (mode == kLane16) {   // one warp: lane l folds the 32 columns of cells l, l + 32, ...
+    if (BITS) {   // fold the G 16-bit columns of each cell (rotated start: no bank conflicts)
+        T = slice + kBitsWords * G;
+        const int rxy = s.rx * s.ry;
+        for (int c = r; c < (int)C; c += G) {
+            const int z = c / rxy, rem = c - z * rxy, x = rem / s.ry, y = rem - x * s.ry;
+            const int* row = cnt + bits_word_of(z, x, y) * G;
+            const int sh = (y & 1) * 16;
+            int sum = 0;
+#pragma unroll 8
+            for (int l = 0; l < G; ++l) sum += (row[(l + c) & (G - 1)] >> sh) & 0xFFFF;
+            T[c] = sum;
+        }
+        *M = T + C;
+    } else if (mode == kLane16) {   // one warp: lane l folds the 32 columns of cells l, l + 32, ...
         T = slice + (C + 1) / 2 * 32;
         for (int c = lane; c < (int)C; c += 32) {
             const int* row = cnt + (c >> 1) * 32;
@@ -724,14 +859,19 @@ __device__ __forceinline__ long long grp_df_adjusted(const TestSpec& s, const in
     return (long long)(grp_sum<G>(acc, red) + 0.5);
 }
 
-// Decision "p > alpha" as "G^2 < crit".  The terms are first evaluated with
-// FP32 logarithms -- each within 3.2e-7 of its own magnitude, CUDA's logf and
-// log1pf being within 1 ulp and the ratio formed from exact 64-bit integers --
-// and summed in FP32: a thread adds at most ceil(C/G) terms and the group tree
-// adds log2(G) levels, each addition erring by at most 6e-8 of the running
-// sum of magnitudes.  G^2 is thus within 2 (3.2e-7 + (ceil(C/G) + log2 G) 6e-8)
-// sum|term| of its exact value (doubled below for margin); only when crit lies
-// inside that band is G^2 recomputed exactly in FP64.
+// Decision "p > alpha" as "G^2 < crit" from FP32 terms under an error bound,
+// all in FP32 (the FP64 pipe of this part is 1/64 of FP32, and every thread
+// of a group would otherwise run the bound in it).  The terms are evaluated
+// with FP32 logarithms -- each within 3.2e-7 of its own magnitude, CUDA's logf
+// and log1pf being within 1 ulp and the ratio formed from exact 64-bit
+// integers -- and summed in FP32: a thread adds at most ceil(C/G) terms and
+// the group tree adds log2(G) levels, each addition erring by at most 6e-8 of
+// the running sum of magnitudes.  G^2 is thus within 2 (3.2e-7 + (ceil(C/G) +
+// log2 G) 6e-8) sum|term| of its exact value; the bound is doubled for margin,
+// formed with upward rounding, and compared against a float bracket [lo, hi]
+// of crit (lo <= crit <= hi): accept when G^2 + err < lo, reject when G^2 -
+// err >= hi (both rounded outward).  Returns 1 (accept), 0 (reject) or -1
+// when the band straddles the bracket and the caller decides exactly.
 //
 // X^2 (stat = kStatX2): each term D^2 / (N_++z N_x+z N_+yz) with D the exact
 // integer difference, formed in FP32 within 6e-7 of itself (three conversions,
@@ -739,8 +879,8 @@ __device__ __forceinline__ long long grp_df_adjusted(const TestSpec& s, const in
 // running sum of magnitudes is the sum itself, and the same summation bound
 // applies without the doubling of G^2.
 template <int G>
-__device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, const int* M, double crit,
-                                           double* red, int stat = kStatG2)
+__device__ __forceinline__ int grp_decide_bound(const TestSpec& s, const int* T, const int* M, float crit_lo,
+                                                float crit_hi, double* red, int stat = kStatG2)
 {
     const int rx = s.rx, ry = s.ry, rxy = rx * ry, C = (int)s.cells;
     const int nz = C / rxy;
@@ -799,16 +939,16 @@ __device__ __forceinline__ bool grp_decide(const TestSpec& s, const int* T, cons
             v.y += r[2 * w + 1];
         }
     }
-    const double per_thread = (double)((s.cells + G - 1) / G);
-    const double levels = (G == 32 ? 5.0 : G == 64 ? 6.0 : G == 128 ? 7.0 : 8.0);
-    const double term_rel = stat == kStatX2 ? 6e-7 : 3.2e-7;
-    const double rel = 2.0 * (term_rel + (per_thread + levels) * 6e-8);
-    const double scale = stat == kStatX2 ? 1.0 : 2.0;   // G^2 = 2 sum
-    const double st = scale * (double)v.x;
-    const double err = scale * rel * (double)v.y * 1.0001 + 1e-9;
-    if (st + err < crit) return true;
-    if (st - err >= crit) return false;
-    return (stat == kStatX2 ? grp_x2_exact<G>(s, T, M, red, nullptr) : grp_g2_exact<G>(s, T, M, red, nullptr)) < crit;
+    const float per_thread = (float)((C + G - 1) / G);   // exact: C < 2^24
+    const float levels = (G == 32 ? 5.0f : G == 64 ? 6.0f : G == 128 ? 7.0f : 8.0f);
+    const float term_rel = stat == kStatX2 ? 6.0e-7f : 3.2e-7f;
+    const float rel = __fmul_ru(2.0f, __fadd_ru(term_rel, __fmul_ru(__fadd_ru(per_thread, levels), 6.0e-8f)));
+    const float scale = stat == kStatX2 ? 1.0f : 2.0f;   // G^2 = 2 sum; exact scaling
+    const float st = scale * v.x;
+    const float err = __fadd_ru(__fmul_ru(__fmul_ru(__fmul_ru(scale, rel), fabsf(v.y)), 1.0001f), 1e-9f);
+    if (__fadd_ru(st, err) < crit_lo) return 1;
+    if (__fadd_rd(st, -err) >= crit_hi) return 0;
+    return -1;
 }
 
 }  // namespace fbn

@@ -24,6 +24,19 @@ constexpr unsigned kStatusEdges = 8u;     // edge list overflow
 constexpr unsigned kStatusTimeout = 16u;  // a bounded device wait gave up
 constexpr unsigned kStatusScratch = 32u;  // a table needed more global scratch than allocated
 constexpr int kMaxArityPairs = 256;       // arity bound of the depth-0 pair epilogue
+// Bit-plane counting: every variable of a test has arity <= kBitsMaxArity (two
+// bit planes per variable) and at most kBitsMaxD conditioning variables.
+constexpr int kBitsMaxArity = 4;
+constexpr int kBitsMaxD = 1;
+constexpr long long kBitsMaxN = 2000000;   // samples within the 16-bit counters of the bit-plane count
+
+// Whether a test can be counted from the bit planes (all arities <= 4, d <= 1,
+// N within the 16-bit counters).  The same rule, applied to an edge's bound on
+// its tables, puts the edge into the bit-plane pool.
+__host__ __device__ __forceinline__ bool bits_shape_ok(int d, int max_arity, long long N)
+{
+    return d <= kBitsMaxD && max_arity <= kBitsMaxArity && N <= kBitsMaxN;
+}
 
 // One learning problem (one data set).  Arrays are device pointers.
 struct ProblemDev {
@@ -49,6 +62,12 @@ struct ProblemDev {
     int32_t* npos;         // [n][n] npos[v][u] = index of u in nbr[v] (u adjacent to v in the snapshot)
     uint8_t* pk;           // [n][pk_ld] samples 4 bits each (depth-1 tensor-core path; arities <= 8)
     int64_t pk_ld;         // ld / 2
+    // bit planes: plane b of variable v, word w = bit b of the values of
+    // samples 32 w .. 32 w + 31 (bit i = sample 32 w + i); planes[(2 v + b) *
+    // plane_ld + w].  plane_ld is a multiple of 4 words; words past the samples
+    // are zero.  Meaningful for variables of arity <= kBitsMaxArity.
+    const uint32_t* planes;
+    int64_t plane_ld;
 };
 
 // One edge i<j of the current depth with its rank space: ranks [0, cnt_i) are
@@ -65,6 +84,7 @@ struct EdgeWork {
 // workers, the others on CTA workers.
 constexpr int kClassWarp = 0;
 constexpr int kClassCta = 1;
+constexpr int kClassBits = 2;   // not an edge class: the small-table class run on the bit-plane pool
 
 // Device-side state of the depth loop.  Per-depth fields are cleared by
 // k_depth_begin; d, active, status and sep_used persist across depths.
@@ -99,6 +119,9 @@ struct DepthCounters {
     unsigned long long nbr_claim;       // vertex claims of the depth-1 tensor-core kernel
     unsigned long long max_total[2];    // largest rank count of an edge per class
     int split[2];                       // sample parts per test per class (1 = whole tests)
+    int bits_ok;                        // 1 while every small-table edge of the depth can be counted from bit
+                                        // planes (k_edges clears it); 1 again for the next depth
+    int pad_bits;
     DepthRecord* rec;                   // per-depth records (persists)
 };
 
@@ -133,6 +156,8 @@ struct ScanClass {
     unsigned long long* base;         // [maxc + 1] first item of pass k
     long long groups[4];              // groups of 32, 64, 128, 256 threads the class's pool runs
     long long smem_ints;              // shared ints of one pool CTA of the class
+    long long groups_bits[4];         // the same for the bit-plane pool (class 0 when every edge qualifies)
+    long long smem_ints_bits;
 };
 
 // Cache of critical values, see fbn_device.cuh.
@@ -142,6 +167,7 @@ struct CritTableDev {
     int cap;
     int dense_n;           // df < dense_n: dense[df], 0 until a test computes it
     double* dense;
+    float2* dense_f;       // df < dense_n: the float bracket (largest float <= crit, smallest >= crit), 0 until set
 };
 
 // Work pool of one depth and one edge class.  Sizes, the depth and the class

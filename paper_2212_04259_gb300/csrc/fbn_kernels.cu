@@ -104,7 +104,7 @@ __device__ __forceinline__ long long binom_sat(const long long* B, int brows, in
 
 __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
                         const int32_t* __restrict__ vtx_first, int total_vertices, int gs_forced, long long gs_edges,
-                        const long long* __restrict__ binom, int brows, long long warp_cells_cap,
+                        const long long* __restrict__ binom, int brows, long long warp_cells_cap, int bits_cells,
                         EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
                         long long edge_cap, DepthCounters* ctr, unsigned long long* __restrict__ hist)
 {
@@ -147,6 +147,11 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
                 cells *= (unsigned long long)P.max_arity;
         }
         const int cls = cells <= (unsigned long long)warp_cells_cap ? kClassWarp : kClassCta;
+        // the small-table class runs on the bit-plane pool only if every one
+        // of its edges qualifies there (all arities <= 4, d <= 1, table bound
+        // within bits_cells)
+        const bool bits = bits_cells > 0 && bits_shape_ok(d, P.max_arity, P.N) && cells <= (unsigned long long)bits_cells;
+        if (__any_sync(0xffffffffu, total > 0 && cls == kClassWarp && !bits) && lane == 0) ctr->bits_ok = 0;
         {   // chunk-count histogram of each class: one atomic per distinct bin in the warp
             const long long bin = total > 0 ? (long long)cls * (kMaxPasses + 1) + chunk_count(total, gs) : -1;
             const unsigned same = __match_any_sync(0xffffffffu, bin);
@@ -246,6 +251,7 @@ __device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long
 // may force a size.
 constexpr double kTestOverhead = 10000.0;
 constexpr double kCyclesPerSample = 8.0;
+constexpr double kCyclesPerSampleBits = 3.0;   // the bit-plane pool
 
 __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double mean_n, int forced_group,
                        long long split_stride, int allow_split)
@@ -260,8 +266,10 @@ __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double me
     const unsigned long long* __restrict__ hist = sc.hist;
     unsigned long long* __restrict__ alive = sc.alive;
     unsigned long long* __restrict__ base = sc.base;
-    const long long g32 = sc.groups[0], g64 = sc.groups[1], g128 = sc.groups[2], g256 = sc.groups[3];
-    const long long smem_ints = sc.smem_ints;
+    const bool bits = cls == kClassWarp && ctr->bits_ok;   // the class runs on the bit-plane pool
+    const long long* grp = bits ? sc.groups_bits : sc.groups;
+    const long long g32 = grp[0], g64 = grp[1], g128 = grp[2], g256 = grp[3];
+    const long long smem_ints = bits ? sc.smem_ints_bits : sc.smem_ints;
     const long long maxc = (long long)ctr->maxc[cls];
     if (ctr->n_edges[cls] == 0) return;
     const int T = blockDim.x;
@@ -301,7 +309,7 @@ __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double me
             for (int k = 0; k < 4; ++k) {
                 const int G = 32 << k;
                 const double rounds = (double)((W + groups[k] - 1) / groups[k]);
-                const double t = rounds * (kTestOverhead + kCyclesPerSample * mean_n / G);
+                const double t = rounds * (kTestOverhead + (bits ? kCyclesPerSampleBits : kCyclesPerSample) * mean_n / G);
                 if (t < best_t) {
                     best_t = t;
                     best = G;
@@ -363,7 +371,8 @@ struct GroupState {
     unsigned ticket;
     int e;
     int go;
-    double crit;
+    double crit;       // exact critical value, 0 until the exact decision needs it
+    float crit_lo, crit_hi;
     int pos[kMaxD];
 };
 
@@ -372,7 +381,7 @@ struct GroupState {
 // successor of the previous rank of the same side); one thread per
 // conditioning variable then resolves its row.  Returns false (uniformly)
 // when the table is over the cell limit.
-template <int G>
+template <int G, bool BITS>
 __device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& w, int d, long long rk, bool fresh,
                                            GroupState& S, const long long* binom, TestSpec& spec, unsigned* status)
 {
@@ -389,19 +398,21 @@ __device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& 
         }
         spec.nrows = d + 2;
         spec.N = P.N;
+        if (BITS) spec.pstride = P.plane_ld >> 2;
     }
     Grp<G>::sync();
-    if (r < d) {
-        const int t = S.pos[r];
-        const int v = P.nbr[(long long)a * P.n + (t < posb ? t : t + 1)];
+    if (r < d + 2) {
+        int v;
+        if (r < d) {
+            const int t = S.pos[r];
+            v = P.nbr[(long long)a * P.n + (t < posb ? t : t + 1)];
+        } else {
+            v = r == d ? w.i : w.j;
+            if (r == d) spec.rx = P.ar[v]; else spec.ry = P.ar[v];
+        }
         spec.rows[r] = P.data + (long long)v * P.ld;
         spec.rad[r] = P.ar[v];
-    } else if (r == d) {
-        spec.rows[d] = P.data + (long long)w.i * P.ld;
-        spec.rad[d] = spec.rx = P.ar[w.i];
-    } else if (r == d + 1) {
-        spec.rows[d + 1] = P.data + (long long)w.j * P.ld;
-        spec.rad[d + 1] = spec.ry = P.ar[w.j];
+        if (BITS && r < kBitsMaxD + 2) spec.prow[r] = reinterpret_cast<const uint4*>(P.planes + (long long)v * 2 * P.plane_ld);
     }
     Grp<G>::sync();
     long long cells = 1;
@@ -422,27 +433,45 @@ template <int G>
 __device__ __forceinline__ int decide_test(const PoolArgs& a, const TestSpec& spec, const int* T, const int* M,
                                            GroupState& S, double* red, unsigned* status)
 {
+    const int nz = (int)spec.cells / (spec.rx * spec.ry);   // cells <= kMaxCells < 2^31: 32-bit
     const long long df = a.df_mode ? grp_df_adjusted<G>(spec, M, red)
-                                   : (long long)(spec.rx - 1) * (spec.ry - 1) * (spec.cells / (spec.rx * spec.ry));
+                                   : (long long)((spec.rx - 1) * (spec.ry - 1)) * nz;
     if (Grp<G>::rank() == 0) {
-        S.crit = df > 0 ? crit_get(a.crit, df, a.alpha, status) : 0.0;
+        // the float bracket of crit when the table has it; else the exact
+        // value (computed and stored on first use) and its bracket
+        float2 f = make_float2(0.0f, 0.0f);
+        if (df > 0 && df < a.crit.dense_n) f = a.crit.dense_f[df];
+        S.crit = 0.0;
+        if (df > 0 && !(f.y > 0.0f)) {
+            const double c = crit_get(a.crit, df, a.alpha, status);
+            S.crit = c;
+            f = make_float2(__double2float_rd(c), __double2float_ru(c));
+        }
+        S.crit_lo = f.x;
+        S.crit_hi = f.y;
         S.tests += 1;   // flushed to the depth counter when the group leaves the pool
     }
     Grp<G>::sync();
     if (df <= 0) return 1;   // p = 1 > alpha
-    return grp_decide<G>(spec, T, M, S.crit, red, a.stat) ? 1 : 0;
+    const int dec = grp_decide_bound<G>(spec, T, M, S.crit_lo, S.crit_hi, red, a.stat);
+    if (dec >= 0) return dec;
+    // the band straddles crit: exact FP64 statistic against the exact value
+    if (Grp<G>::rank() == 0 && S.crit == 0.0) S.crit = crit_get(a.crit, df, a.alpha, status);
+    Grp<G>::sync();
+    const double ex = a.stat == kStatX2 ? grp_x2_exact<G>(spec, T, M, red, nullptr) : grp_g2_exact<G>(spec, T, M, red, nullptr);
+    return ex < S.crit ? 1 : 0;
 }
 
 // Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
-template <int G>
+template <int G, bool BITS>
 __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w, long long rk,
                                         bool fresh, GroupState& S, TestSpec& spec, int* slice, long long slice_ints,
                                         int* gtab, double* red)
 {
     unsigned* status = &a.ctr->status;
-    if (!setup_rank<G>(P, w, d, rk, fresh, S, a.binom, spec, status)) return -1;
+    if (!setup_rank<G, BITS>(P, w, d, rk, fresh, S, a.binom, spec, status)) return -1;
     int* M = nullptr;
-    const int* T = grp_table<G>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
+    const int* T = grp_table<G, BITS>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
     if (!T) {   // the global scratch is too small: the host grows it and starts over
         if (Grp<G>::rank() == 0) {
             atomicOr(status, kStatusScratch);
@@ -458,7 +487,7 @@ __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemD
 // bounds) of rank rk into the test's global table; the part that finishes last
 // copies the table into shared memory (L2 reads), zeroes it, decides and
 // lowers the edge's rank.  Returns 1 when this group decided an acceptance.
-template <int G>
+template <int G, bool BITS>
 __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w,
                                               long long rk, int split, GroupState& S, TestSpec& spec, int* slice,
                                               long long slice_ints, int* gtab, double* red,
@@ -470,17 +499,22 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
     if (r == 0) S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
     Grp<G>::sync();
     bool ready = false;   // spec holds this rank's table shape (uniform over the group)
-    if (S.go && setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) {
+    if (S.go && setup_rank<G, BITS>(P, w, d, rk, true, S, a.binom, spec, status)) {
         ready = true;
         const long long N = P.N;
-        const long long lo = (N * S.part / split) & ~15LL;
-        const long long hi = S.part == split - 1 ? N : ((N * (S.part + 1) / split) & ~15LL);
-        if (r < d + 2) spec.rows[r] += lo;
+        // part bounds on 128-sample boundaries: whole 16-byte vectors of the
+        // byte rows and whole uint4 groups of the bit planes
+        const long long lo = (N * S.part / split) & ~127LL;
+        const long long hi = S.part == split - 1 ? N : ((N * (S.part + 1) / split) & ~127LL);
+        if (r < d + 2) {
+            spec.rows[r] += lo;
+            if (BITS && r < kBitsMaxD + 2) spec.prow[r] += lo >> 7;
+        }
         Grp<G>::sync();
         if (r == 0) spec.N = (int)(hi - lo);
         Grp<G>::sync();
         int* M = nullptr;
-        const int* T = grp_table<G>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
+        const int* T = grp_table<G, BITS>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
         if (!T) {
             if (r == 0) {
                 atomicOr(status, kStatusScratch);
@@ -500,7 +534,7 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
     // the table's shape only (cells, radices), which this part's own setup
     // left in spec when it counted
     __threadfence();
-    if (!ready && !setup_rank<G>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
+    if (!ready && !setup_rank<G, BITS>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
     const long long C = spec.cells;
     int* Tl = slice;
     for (long long c = r; c < C; c += G) {
@@ -526,7 +560,7 @@ struct PoolShared {
     unsigned long long base[kBaseSmem];
 };
 
-template <int G>
+template <int G, bool BITS = false>
 __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShared& sh)
 {
     constexpr int NG = kTestThreads / G;   // groups per CTA
@@ -558,7 +592,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     for (;;) {
         if (r == 0) {
             const unsigned long long wi = atomicAdd(next_item, 1ULL);
-            const unsigned long long w = wi / (unsigned long long)split;
+            const unsigned long long w = split == 1 ? wi : wi / (unsigned long long)split;
             S.item = w;
             S.part = (int)(wi - w * (unsigned long long)split);
             S.e = -1;
@@ -584,8 +618,8 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
         const ProblemDev& P = a.probs[w.prob];
         const long long r0 = S.r0, r1 = S.r1;
         if (split > 1) {   // single-rank items (gs = 1, no edge above kMaxPasses ranks)
-            const int res = run_split_part<G>(a, d, P, w, r0, split, S, spec, slice, slice_ints, gtab, sh.red,
-                                              &min_accept[e]);
+            const int res = run_split_part<G, BITS>(a, d, P, w, r0, split, S, spec, slice, slice_ints, gtab, sh.red,
+                                                    &min_accept[e]);
             if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)r0);
             Grp<G>::sync();
             continue;
@@ -594,7 +628,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
             if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&min_accept[e]);
             Grp<G>::sync();
             if (!S.go) break;
-            const int res = run_rank<G>(a, d, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, sh.red);
+            const int res = run_rank<G, BITS>(a, d, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, sh.red);
             if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)rk);
             if (res != 0) break;
         }
@@ -611,18 +645,40 @@ __device__ __forceinline__ void tests_done(const DepthCounters* ctr)
         if (DepthRecord* r = depth_rec(ctr, ctr->d)) atomicMax(&r->t_tests_end, gtime());
 }
 
-// Small-table class: the group size k_scan chose for this depth.
+// Small-table class: the group size k_scan chose for this depth; byte
+// histograms (the depth's class when some edge cannot use the bit planes).
 __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
 {
     pdl_enter();
     extern __shared__ int smem[];
     __shared__ PoolShared sh;
-    if (!a.ctr->active) return;
+    if (!a.ctr->active || a.ctr->bits_ok) return;
     switch (a.ctr->gsel) {
         case 32: pool_body<32>(a, smem, sh); break;
         case 64: pool_body<64>(a, smem, sh); break;
         case 128: pool_body<128>(a, smem, sh); break;
         default: pool_body<kTestThreads>(a, smem, sh); break;
+    }
+    tests_done(a.ctr);
+}
+
+// Small-table class counted from bit planes: the depth's class when every
+// edge qualifies (k_edges); otherwise k_pool_small runs it.  CTAs per SM: 4
+// (64 registers a thread; its 36 KB of shared memory allow it).
+#ifndef FBN_BITS_CTAS
+#define FBN_BITS_CTAS 4
+#endif
+__global__ void __launch_bounds__(kTestThreads, FBN_BITS_CTAS) k_pool_bits(PoolArgs a)
+{
+    pdl_enter();
+    extern __shared__ int smem[];
+    __shared__ PoolShared sh;
+    if (!a.ctr->active || !a.ctr->bits_ok || a.ctr->n_edges[kClassWarp] == 0) return;
+    switch (a.ctr->gsel) {
+        case 32: pool_body<32, true>(a, smem, sh); break;
+        case 64: pool_body<64, true>(a, smem, sh); break;
+        case 128: pool_body<128, true>(a, smem, sh); break;
+        default: pool_body<kTestThreads, true>(a, smem, sh); break;
     }
     tests_done(a.ctr);
 }
@@ -658,7 +714,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
         const EdgeWork w = a.edges[cb + e];
         const ProblemDev& P = a.probs[w.prob];
         for (long long rk = 0; rk < w.total; ++rk) {
-            const int res = run_rank<kTestThreads>(a, d, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
+            const int res = run_rank<kTestThreads, false>(a, d, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
             if (res == 1 && threadIdx.x == 0) a.min_accept[cb + e] = (unsigned long long)rk;
             if (res != 0) break;
         }
@@ -761,6 +817,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
         ctr->nbr_claim = 0;
         ctr->max_total[0] = ctr->max_total[1] = 0;
         ctr->split[0] = ctr->split[1] = 1;
+        ctr->bits_ok = 1;
         ctr->d = next;
         __threadfence();
         ctr->active = stop ? 0 : 1;
@@ -789,6 +846,7 @@ __global__ void k_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop)
 
 // --------------------------------------------------------------------------
 // Explicit tests (fbn_ci_test / fbn_ci_table): exact FP64 G^2 and p-value.
+template <bool BITS>
 __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __restrict__ prob,
                                                            const CiTestDesc* __restrict__ tests, int ntests,
                                                            double* __restrict__ out, int32_t* table_out,
@@ -806,14 +864,13 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
         const CiTestDesc& q = tests[t];
         const int d = q.d;
         long long cells = 1;
-        for (int k = 0; k < d; ++k) {
-            spec.rows[k] = P.data + (long long)q.z[k] * P.ld;
-            spec.rad[k] = P.ar[q.z[k]];
+        for (int k = 0; k < d + 2; ++k) {
+            const int v = k < d ? q.z[k] : k == d ? q.x : q.y;
+            spec.rows[k] = P.data + (long long)v * P.ld;
+            spec.rad[k] = P.ar[v];
+            if (BITS && k < kBitsMaxD + 2) spec.prow[k] = reinterpret_cast<const uint4*>(P.planes + (long long)v * 2 * P.plane_ld);
         }
-        spec.rows[d] = P.data + (long long)q.x * P.ld;
-        spec.rad[d] = P.ar[q.x];
-        spec.rows[d + 1] = P.data + (long long)q.y * P.ld;
-        spec.rad[d + 1] = P.ar[q.y];
+        spec.pstride = P.plane_ld >> 2;
         spec.nrows = d + 2;
         spec.rx = P.ar[q.x];
         spec.ry = P.ar[q.y];
@@ -827,7 +884,7 @@ __global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __r
     if (!s_ok) return;
     int* gtab = gscratch ? gscratch + (long long)t * gscratch_ints : nullptr;
     int* M = nullptr;
-    const int* T = grp_table<kTestThreads>(spec, smem, smem_ints, gtab, gscratch_ints, &M);
+    const int* T = grp_table<kTestThreads, BITS>(spec, smem, smem_ints, gtab, gscratch_ints, &M);
     if (!T) {
         if (threadIdx.x == 0) atomicOr(status, kStatusTooBig);
         return;
@@ -874,14 +931,14 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
                   int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
-                  long long warp_cells_cap,
+                  long long warp_cells_cap, int bits_cells,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st)
 {
     const int warps = 8;
     launch_pdl(k_edges, dim3((total_vertices + warps - 1) / warps), dim3(warps * 32), 0, st, probs, vtx_prob,
-               vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, edges, min_accept,
-               edge_cap, ctr, hist);
+               vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, bits_cells, edges,
+               min_accept, edge_cap, ctr, hist);
 }
 
 void launch_order(const EdgeWork* edges, long long edge_cap, int nclass, DepthCounters* ctr, const ScanClass* sc,
@@ -898,6 +955,11 @@ void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaSt
 {
     if (cls == kClassWarp) launch_pdl(k_pool_small, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
     else launch_pdl(k_pool_big, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
+}
+
+void launch_pool_bits(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st)
+{
+    launch_pdl(k_pool_bits, dim3(grid), dim3(kTestThreads), smem_bytes, st, a);
 }
 
 void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st)
@@ -931,11 +993,11 @@ void set_pdl(bool on)
 
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
-                     size_t smem_bytes, int stat, int df_mode, cudaStream_t st)
+                     size_t smem_bytes, int stat, int df_mode, bool bits, cudaStream_t st)
 {
-    k_ci_tests<<<ntests, kTestThreads, smem_bytes, st>>>(prob, tests, ntests, out, table_out, gscratch,
-                                                         gscratch_ints, status, (int)(smem_bytes / 4), stat,
-                                                         df_mode);
+    auto kern = bits ? k_ci_tests<true> : k_ci_tests<false>;
+    kern<<<ntests, kTestThreads, smem_bytes, st>>>(prob, tests, ntests, out, table_out, gscratch, gscratch_ints,
+                                                   status, (int)(smem_bytes / 4), stat, df_mode);
 }
 
 cudaError_t set_kernel_smem(size_t max_smem)
@@ -944,14 +1006,18 @@ cudaError_t set_kernel_smem(size_t max_smem)
     const int b = (int)max_smem;
     if ((e = cudaFuncSetAttribute(k_pool_small, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k_pool_big, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    if ((e = cudaFuncSetAttribute(k_pool_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    return cudaFuncSetAttribute(k_ci_tests, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if ((e = cudaFuncSetAttribute(k_ci_tests<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
+    return cudaFuncSetAttribute(k_ci_tests<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
 int pool_blocks_per_sm(int cls, size_t smem_bytes)
 {
     int nb = 0;
-    if (cls == kClassWarp)
+    if (cls == kClassBits)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool_bits, kTestThreads, smem_bytes);
+    else if (cls == kClassWarp)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool_small, kTestThreads, smem_bytes);
     else
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_pool_big, kTestThreads, smem_bytes);

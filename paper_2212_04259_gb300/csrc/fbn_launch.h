@@ -19,7 +19,7 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
                      int total_vertices, DepthCounters* ctr, cudaStream_t st);
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
                   int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
-                  long long warp_cells_cap,
+                  long long warp_cells_cap, int bits_cells,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st);
 // Ordering of the depth's edges, one CTA per class (nclass = 1: the small-
@@ -28,6 +28,7 @@ void launch_order(const EdgeWork* edges, long long edge_cap, int nclass, DepthCo
                   unsigned long long* cursor0, unsigned long long* cursor1, int32_t* sorted, double mean_n,
                   int forced_group, long long split_stride, int allow_split, int grid, cudaStream_t st);
 void launch_pool(const PoolArgs& a, int cls, int grid, size_t smem_bytes, cudaStream_t st);
+void launch_pool_bits(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t st);
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
                   long long edge_cap, const long long* binom, int32_t* sep_pool, long long sep_cap,
@@ -40,7 +41,7 @@ void launch_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop, cudaStream
 void set_pdl(bool on);
 void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
-                     size_t smem_bytes, int stat, int df_mode, cudaStream_t st);
+                     size_t smem_bytes, int stat, int df_mode, bool bits, cudaStream_t st);
 cudaError_t set_kernel_smem(size_t max_smem);
 // Sets the message fbn_last_error(NULL) returns.
 void fbn_internal_set_error(const char* msg);

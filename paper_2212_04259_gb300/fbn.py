@@ -24,6 +24,7 @@ DEPTH1 = {"auto": 0, "pool": 1, "tensor": 2}
 STATISTIC = {"g2": 0, "x2": 1}
 DF_MODE = {"fixed": 0, "adjusted": 1}
 LOOP = {"device": 0, "host": 1}
+COUNT = {"auto": 0, "hist": 1, "bits": 2}
 MAX_DEPTHS = 64
 
 # Every symbol include/fbn.h declares.
@@ -43,7 +44,7 @@ class Options(C.Structure):
     _fields_ = [("form", C.c_int32), ("group_size", C.c_int32), ("depth0", C.c_int32),
                 ("device", C.c_int32), ("group_threads", C.c_int32), ("wait_limit", C.c_int32),
                 ("depth1", C.c_int32), ("statistic", C.c_int32), ("df_mode", C.c_int32),
-                ("loop", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("loop", C.c_int32), ("count", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Stats(C.Structure):
@@ -151,7 +152,7 @@ def _as_u8_2d(data):
 
 def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-1,
                group_threads=0, wait_limit=0, depth1="auto", statistic="g2", df="fixed",
-               loop="device") -> Handle:
+               loop="device", count="auto") -> Handle:
     """Upload variable-major uint8 data [n_vars][n_samples] (numpy, or torch host/device)."""
     data, (n, N) = _as_u8_2d(data)
     ar = np.ascontiguousarray(arities, dtype=np.uint8)
@@ -159,7 +160,7 @@ def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-
         raise ValueError("arities must have one entry per variable")
     o = Options(form=FORMS[form], group_size=group_size, depth0=DEPTH0[depth0], device=device,
                 group_threads=group_threads, wait_limit=wait_limit, depth1=DEPTH1[depth1],
-                statistic=STATISTIC[statistic], df_mode=DF_MODE[df], loop=LOOP[loop])
+                statistic=STATISTIC[statistic], df_mode=DF_MODE[df], loop=LOOP[loop], count=COUNT[count])
     out = C.c_void_p()
     rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
     _check(rc)

@@ -78,6 +78,9 @@ def test_create_rejects_bad_arguments_before_touching_a_device(built):
     ar = np.array([2, 2], np.uint8)
     rc = f.fbn.lib().fbn_create(f.fbn._ptr(data), 2, 10, f.fbn._ptr(ar), f.fbn.C.byref(o), f.fbn.C.byref(out))
     assert rc == -1 and "bad loop" in f.fbn_last_error(None)
+    o = f.fbn.Options(device=-1, count=3)                    # no such counting strategy
+    rc = f.fbn.lib().fbn_create(f.fbn._ptr(data), 2, 10, f.fbn._ptr(ar), f.fbn.C.byref(o), f.fbn.C.byref(out))
+    assert rc == -1 and "bad count" in f.fbn_last_error(None)
 
 
 def test_no_cpu_fallback_without_gpu(built):
