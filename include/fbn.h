@@ -99,6 +99,11 @@ typedef struct fbn_stats {
     int64_t gram_samples;                   /* padded samples of the Gram */
     int64_t test_samples[FBN_MAX_DEPTHS];   /* sum over the tests_oracle[d] tests of their data set's N
                                                (in a batch each test counts its own problem's samples) */
+    int64_t popc_work[FBN_MAX_DEPTHS];      /* counting work executed from bit planes: cells x 32-sample words
+                                               (one POPC each) over the tests so counted, redundant ones included */
+    int64_t smem_updates[FBN_MAX_DEPTHS];   /* counting work executed by byte histograms: samples of the tests so
+                                               counted (one shared-memory reduction each, or a global one for the
+                                               largest tables), redundant ones included */
 } fbn_stats;
 
 typedef struct fbn_handle fbn_handle;
@@ -224,6 +229,20 @@ const char* fbn_last_error(const fbn_handle* h);
 
 /* fbn_destroy -- free the handle and its device memory (NULL is a no-op). */
 void fbn_destroy(fbn_handle* h);
+
+/* fbn_measure_unit_rates -- measured throughput of the two units that bound
+ * the contingency counts, for reporting the counting kernels against a
+ * measured peak (the paper has no counterpart: a measurement utility).
+ *   device : CUDA device ordinal, -1 = the current device (restored after).
+ *   out    : host, n_out >= 4 doubles:
+ *            out[0] shared-memory 32-bit reductions per second (red.shared.add,
+ *                   each thread on its own column: no conflicts), whole device;
+ *            out[1] POPC per second, whole device;
+ *            out[2] SMs;  out[3] the device's reported SM clock (Hz).
+ * Runs two kernels of a few milliseconds each, allocates a few kilobytes and
+ * synchronises.  Errors: FBN_EINVAL (out NULL or n_out < 4), FBN_ENOMEM,
+ * FBN_ECUDA, with the reason in fbn_last_error(NULL). */
+int fbn_measure_unit_rates(int32_t device, double* out, int32_t n_out);
 
 /* fbn_ci_test_noalloc -- the test of fbn_ci_test for callers that cannot
  * allocate device memory: a process whose device memory belongs to another

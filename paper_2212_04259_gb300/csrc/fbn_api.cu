@@ -1122,6 +1122,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         stats.tests[d] = r.tests;
         stats.tests_oracle[d] = r.tests_oracle;
         stats.test_samples[d] = r.test_samples;
+        stats.popc_work[d] = r.popc_work;
+        stats.smem_updates[d] = r.smem_updates;
         stats.removed[d] = r.removed;
         const unsigned long long next = d + 1 < kMaxDepthRecords ? ws.h_rec[d + 1].t_begin : 0;
         const unsigned long long end = next > r.t_begin ? next : r.t_end;

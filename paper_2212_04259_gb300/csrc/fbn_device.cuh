@@ -537,7 +537,9 @@ __device__ __forceinline__ void count_dispatch(const TestSpec& s, int* base)
 // two to a register (32 registers, indices known at compile time), so the
 // sample loop touches no shared memory.  The strata and x loops stop at the
 // test's arities; the y loop always runs its 4 values (a value the variable
-// cannot take pops zero), which keeps the innermost loop free of branches.
+// cannot take pops zero), which keeps the innermost loop free of branches
+// (measured: skipping them by predication, or one loop copy per r_y, ran
+// slower -- the kernel is sensitive to its code footprint).
 // The one partial word at the end of the samples is peeled off with its
 // validity mask.  A counter grows by at most 32 per word and a thread sees at
 // most ceil(N / 32 / G) words: below 2^16 while N <= kBitsMaxN.
@@ -595,7 +597,8 @@ __device__ __forceinline__ void bits_count(unsigned* acc, const BitsWord& b, uns
 
 // cnt: this thread's column of kBitsWords counter words with stride G
 // (bits_word_of layout).  Not inlined: one call per test, and the sample loop
-// gets the kernel's whole register budget.
+// gets the kernel's whole register budget.  One body for every table shape:
+// copies of the loop per arity (measured) ran slower than the POPC they save.
 template <int G>
 __device__ __noinline__ void count_bits(const TestSpec& s, int* cnt)
 {
@@ -624,7 +627,8 @@ __device__ __noinline__ void count_bits(const TestSpec& s, int* cnt)
             cur = nxt;
         }
     }
-    if (w == full && full < nw) bits_count(acc, bits_load(xr, yr, zr, ps, w, d), (1u << (s.N & 31)) - 1u, d, rz, rx);
+    if (w == full && full < nw)
+        bits_count(acc, bits_load(xr, yr, zr, ps, w, d), (1u << (s.N & 31)) - 1u, d, rz, rx);
 #pragma unroll
     for (int k = 0; k < kBitsWords; ++k)
         if ((k >> 3) < rz) cnt[k * G] = (int)acc[k];

@@ -93,6 +93,8 @@ constexpr int kMaxDepthRecords = 64;
 struct DepthRecord {
     long long edges, tests, tests_oracle, removed;
     long long test_samples;   // sum of N over the sequential order's tests (their problems' sample counts)
+    long long popc_work;      // popcounts of the tests counted from bit planes (cells x 32-sample words)
+    long long smem_updates;   // shared-memory histogram updates (samples of the tests counted by histogram)
     // device clock (ns): depth start (snapshot), test kernels start and end,
     // depth end; 0 where a kernel of the depth did not run
     unsigned long long t_begin, t_tests, t_tests_end, t_end;
@@ -106,6 +108,8 @@ struct DepthCounters {
     unsigned long long tests;           // CI tests executed
     unsigned long long tests_oracle;    // tests of the sequential order (gs = 1)
     unsigned long long test_samples;    // sum over those tests of their problem's N
+    unsigned long long popc_work;       // executed counting work: popcounts (bit planes)
+    unsigned long long smem_updates;    // executed counting work: histogram updates (samples)
     unsigned long long removed;         // edges removed
     unsigned long long max_cells[2];    // upper bound of table cells per class
     unsigned long long sep_used;        // separating-set pool entries in use (persists)

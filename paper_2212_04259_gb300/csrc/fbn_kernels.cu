@@ -315,7 +315,7 @@ __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double me
                     best = G;
                 }
             }
-            ctr->gsel = forced_group ? forced_group : best;
+            ctr->gsel = bits ? 32 : forced_group ? forced_group : best;   // the bit-plane pool: warp groups
         }
         // sample split: few single-rank tests against the groups of the class
         const int G = cls == 0 ? ctr->gsel : kTestThreads;
@@ -366,6 +366,7 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, 
 struct GroupState {
     long long r0, r1;
     unsigned long long tests;
+    unsigned long long popc_work, smem_updates;   // counting work done, flushed with tests
     unsigned long long item;   // split tests: the test's item and this group's part
     int part;
     unsigned ticket;
@@ -463,6 +464,16 @@ __device__ __forceinline__ int decide_test(const PoolArgs& a, const TestSpec& sp
 }
 
 // Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
+// Counting work of one table (rank 0): C popcounts per 32-sample word from
+// bit planes, or one shared-memory update per sample by histogram.
+template <int G, bool BITS>
+__device__ __forceinline__ void note_work(GroupState& S, const TestSpec& spec)
+{
+    if (Grp<G>::rank() != 0) return;
+    if (BITS) S.popc_work += (unsigned long long)spec.cells * (unsigned long long)((spec.N + 31) >> 5);
+    else S.smem_updates += (unsigned long long)spec.N;
+}
+
 template <int G, bool BITS>
 __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w, long long rk,
                                         bool fresh, GroupState& S, TestSpec& spec, int* slice, long long slice_ints,
@@ -479,6 +490,7 @@ __device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemD
         }
         return -1;
     }
+    note_work<G, BITS>(S, spec);
     grp_marginals<G>(spec, T, M);
     return decide_test<G>(a, spec, T, M, S, red, status);
 }
@@ -521,6 +533,7 @@ __device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const Probl
                 atomicMax(&a.ctr->need_cells, (int)spec.cells);
             }
         } else {
+            note_work<G, BITS>(S, spec);
             for (long long c = r; c < spec.cells; c += G)
                 if (T[c]) atomicAdd(Tg + c, T[c]);
         }
@@ -586,7 +599,7 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
     const unsigned long long* base = base_in_smem ? sh.base : a.base;
     GroupState& S = sh.st[g];
     TestSpec& spec = sh.spec[g];
-    if (r == 0) S.tests = 0;
+    if (r == 0) S.tests = S.popc_work = S.smem_updates = 0;
     const int split = ctr->split[a.cls] > 1 ? ctr->split[a.cls] : 1;
 
     for (;;) {
@@ -635,6 +648,8 @@ __device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShar
         Grp<G>::sync();
     }
     if (r == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
+    if (r == 0 && S.popc_work) atomicAdd(&a.ctr->popc_work, S.popc_work);
+    if (r == 0 && S.smem_updates) atomicAdd(&a.ctr->smem_updates, S.smem_updates);
 }
 
 // The end of a test CTA in the depth's record (the latest over CTAs).
@@ -663,8 +678,10 @@ __global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
 }
 
 // Small-table class counted from bit planes: the depth's class when every
-// edge qualifies (k_edges); otherwise k_pool_small runs it.  CTAs per SM: 4
-// (64 registers a thread; its 36 KB of shared memory allow it).
+// edge qualifies (k_edges); otherwise k_pool_small runs it.  Warp groups only:
+// the fastest group size at every measured depth, and one copy of the code (the
+// kernel is sensitive to its code footprint).  CTAs per SM: 4 (64 registers a
+// thread; its 36 KB of shared memory allow it).
 #ifndef FBN_BITS_CTAS
 #define FBN_BITS_CTAS 4
 #endif
@@ -674,12 +691,7 @@ __global__ void __launch_bounds__(kTestThreads, FBN_BITS_CTAS) k_pool_bits(PoolA
     extern __shared__ int smem[];
     __shared__ PoolShared sh;
     if (!a.ctr->active || !a.ctr->bits_ok || a.ctr->n_edges[kClassWarp] == 0) return;
-    switch (a.ctr->gsel) {
-        case 32: pool_body<32, true>(a, smem, sh); break;
-        case 64: pool_body<64, true>(a, smem, sh); break;
-        case 128: pool_body<128, true>(a, smem, sh); break;
-        default: pool_body<kTestThreads, true>(a, smem, sh); break;
-    }
+    pool_body<32, true>(a, smem, sh);   // warp groups only (k_scan sets gsel = 32): one copy of the code
     tests_done(a.ctr);
 }
 
@@ -709,7 +721,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
     const long long E = (long long)ctr->n_edges[a.cls];
     const long long cb = class_base(ctr, a.cls, a.edge_cap);
     int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
-    if (threadIdx.x == 0) S.tests = 0;
+    if (threadIdx.x == 0) S.tests = S.popc_work = S.smem_updates = 0;
     for (long long e = blockIdx.x; e < E; e += gridDim.x) {
         const EdgeWork w = a.edges[cb + e];
         const ProblemDev& P = a.probs[w.prob];
@@ -721,6 +733,7 @@ __global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
         __syncthreads();
     }
     if (threadIdx.x == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
+    if (threadIdx.x == 0 && S.smem_updates) atomicAdd(&a.ctr->smem_updates, S.smem_updates);
     tests_done(ctr);
 }
 
@@ -803,6 +816,8 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
             rec[d].tests = (long long)ctr->tests;
             rec[d].tests_oracle = (long long)ctr->tests_oracle;
             rec[d].test_samples = (long long)ctr->test_samples;
+            rec[d].popc_work = (long long)ctr->popc_work;
+            rec[d].smem_updates = (long long)ctr->smem_updates;
             rec[d].removed = (long long)ctr->removed;
             rec[d].t_end = gtime();
         }
@@ -811,7 +826,7 @@ __global__ void k_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth,
                           next >= kMaxDepthRecords;
         for (int c = 0; c < 2; ++c)
             ctr->n_edges[c] = ctr->maxc[c] = ctr->next_item[c] = ctr->total_items[c] = ctr->max_cells[c] = 0;
-        ctr->tests = ctr->tests_oracle = ctr->removed = ctr->test_samples = 0;
+        ctr->tests = ctr->tests_oracle = ctr->removed = ctr->test_samples = ctr->popc_work = ctr->smem_updates = 0;
         ctr->gsel = 0;
         ctr->adj_ends = 0;
         ctr->nbr_claim = 0;

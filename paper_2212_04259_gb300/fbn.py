@@ -31,7 +31,7 @@ MAX_DEPTHS = 64
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_orient_cpdag", "fbn_get_stats",
            "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
-           "fbn_update_data")
+           "fbn_update_data", "fbn_measure_unit_rates")
 
 
 class FbnError(RuntimeError):
@@ -53,7 +53,8 @@ class Stats(C.Structure):
                 ("tests_oracle", C.c_int64 * MAX_DEPTHS), ("removed", C.c_int64 * MAX_DEPTHS),
                 ("ms", C.c_double * MAX_DEPTHS), ("test_ms", C.c_double * MAX_DEPTHS),
                 ("gram_ms", C.c_double), ("gram_rows", C.c_int64), ("gram_samples", C.c_int64),
-                ("test_samples", C.c_int64 * MAX_DEPTHS)]
+                ("test_samples", C.c_int64 * MAX_DEPTHS), ("popc_work", C.c_int64 * MAX_DEPTHS),
+                ("smem_updates", C.c_int64 * MAX_DEPTHS)]
 
 
 _lock = threading.Lock()
@@ -99,6 +100,8 @@ def lib():
         L.fbn_update_data.argtypes = [p, p]
         L.fbn_pairwise_counts.restype = C.c_int
         L.fbn_pairwise_counts.argtypes = [p, p, i64]
+        L.fbn_measure_unit_rates.restype = C.c_int
+        L.fbn_measure_unit_rates.argtypes = [i32, p, i32]
         L.fbn_ci_test_noalloc.restype = C.c_int
         L.fbn_ci_test_noalloc.argtypes = [p, i64, i32, i64, p, i32, i32, p, i32, p, p, p]
         _lib = L
@@ -289,12 +292,21 @@ def fbn_get_stats(h: Handle) -> dict:
             "tests": list(s.tests[:d]), "tests_oracle": list(s.tests_oracle[:d]),
             "removed": list(s.removed[:d]), "ms": list(s.ms[:d]), "test_ms": list(s.test_ms[:d]),
             "gram_ms": float(s.gram_ms), "gram_rows": int(s.gram_rows), "gram_samples": int(s.gram_samples),
-            "test_samples": list(s.test_samples[:d])}
+            "test_samples": list(s.test_samples[:d]), "popc_work": list(s.popc_work[:d]),
+            "smem_updates": list(s.smem_updates[:d])}
 
 
 def fbn_last_error(h: Handle | None = None) -> str:
     m = lib().fbn_last_error(h.ptr if h is not None else None)
     return m.decode() if m else ""
+
+
+def fbn_measure_unit_rates(device: int = -1) -> dict:
+    """Measured shared-memory reduction and POPC throughput of the device."""
+    out = np.zeros(4, dtype=np.float64)
+    _check(lib().fbn_measure_unit_rates(int(device), _ptr(out), 4))
+    return {"smem_red_per_s": float(out[0]), "popc_per_s": float(out[1]), "sms": int(out[2]),
+            "sm_clock_hz": float(out[3])}
 
 
 def fbn_destroy(h: Handle) -> None:
