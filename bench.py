@@ -82,6 +82,9 @@ def parse():
                     help="depth-1 counting: tensor-core neighbourhood product or work pool")
     ap.add_argument("--statistic", choices=["g2", "x2"], default="g2", help="CI statistic (G^2 or Pearson X^2)")
     ap.add_argument("--df", choices=["fixed", "adjusted"], default="fixed", help="degrees of freedom of each test")
+    ap.add_argument("--tune", choices=["auto", "off"], default="auto",
+                    help="autotune the counting per depth before the warm-up (fbn_autotune; untimed), or keep the "
+                         "fixed rules")
     ap.add_argument("--count", choices=["auto", "hist", "bits"], default="auto",
                     help="table counting: bit planes for small tables (auto), byte histograms only, bit planes "
                          "wherever they fit")
@@ -112,7 +115,7 @@ def workload_config(name, w, args):
         cfg.update(statistic=args.statistic, df=args.df, loop=args.loop)
     if args.loop != "device":
         cfg.update(loop=args.loop)
-    cfg.update(count=args.count)
+    cfg.update(count=args.count, tune=args.tune)
     if w["kind"] == "single":
         n, N = w["data"].shape
         cfg.update(n_vars=n, n_samples=N, alpha=w["alpha"], max_depth=w["max_depth"],
@@ -424,6 +427,9 @@ def main():
             F.fbn_learn_skeleton_batch(handles, w["alpha"], w["max_depth"], adj_out=outs)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device="cuda")  # 256 MB > L2
+    tuning = None
+    if args.tune == "auto" and args.form == "pool":   # choices by measurement, before the warm-up (untimed)
+        tuning = F.fbn_autotune(handles, w["alpha"], w["max_depth"])
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -637,7 +643,7 @@ def main():
                 "config": workload_config(name, w, args), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(st["launches"]) * args.steps, "roofline": roofline,
                 "roofline_hbm": roofline_hbm, "roofline_smem": roofline_smem, "roofline_gram": roofline_gram,
-                "unit_rates": rates,
+                "unit_rates": rates, "tuning": tuning,
                 "cpu_baseline": cpu, "plain_form": plain,
                 "tests_per_step": {"oracle_equivalent": tests, "executed": sum(st["tests"]),
                                    "per_depth_oracle": st["tests_oracle"]},

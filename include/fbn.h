@@ -58,6 +58,11 @@ extern "C" {
 #define FBN_COUNT_HIST 1   /* every table by the byte histogram (shared-memory reductions, or a global table) */
 #define FBN_COUNT_BITS 2   /* bit planes for every test that qualifies and fits shared memory, whatever its size */
 
+#define FBN_TUNE_OFF  0    /* fixed rules: bit planes where every small table qualifies, group size by a cost model,
+                              depth 0 on the Gram by problem size */
+#define FBN_TUNE_AUTO 1    /* the first skeleton call on a workload shape runs fbn_autotune (or reuses its result
+                              for this device and shape from earlier in the process) and applies its choices */
+
 #define FBN_LOOP_DEVICE 0  /* the depths after any launched directly run as one CUDA graph whose while node the
                               device drives (no host round trip between depths) */
 #define FBN_LOOP_HOST   1  /* the same kernels, one depth at a time from the host, which reads the loop flag
@@ -79,7 +84,8 @@ typedef struct fbn_options {
     int32_t loop;        /* FBN_LOOP_DEVICE (default) or FBN_LOOP_HOST: who drives the depth loop */
     int32_t count;       /* FBN_COUNT_*: how contingency tables are counted (pool form and explicit tests; the
                             plain form always uses byte histograms) */
-    int32_t reserved[5]; /* must be zero */
+    int32_t tune;        /* FBN_TUNE_OFF (default) or FBN_TUNE_AUTO */
+    int32_t reserved[4]; /* must be zero */
 } fbn_options;
 
 /* Per-depth counters of the last fbn_learn_skeleton call. */
@@ -105,6 +111,18 @@ typedef struct fbn_stats {
                                                counted (one shared-memory reduction each, or a global one for the
                                                largest tables), redundant ones included */
 } fbn_stats;
+
+/* The choices of fbn_autotune, per depth of the skeleton. */
+typedef struct fbn_tuning {
+    int32_t depths;                            /* depths measured */
+    int32_t depth0;                            /* FBN_DEPTH0_GRAM or FBN_DEPTH0_HIST: how depth 0 counts */
+    int32_t group_threads[FBN_MAX_DEPTHS];     /* threads per test of the small-table class at depth d (32..256) */
+    int32_t count[FBN_MAX_DEPTHS];             /* FBN_COUNT_HIST or FBN_COUNT_BITS at depth d */
+    double  ms_fixed;                          /* skeleton time under the fixed rules (device events, ms) */
+    double  ms_tuned;                          /* skeleton time under the choices */
+    int32_t candidates;                        /* configurations timed */
+    int32_t reserved;
+} fbn_tuning;
 
 typedef struct fbn_handle fbn_handle;
 
@@ -190,6 +208,21 @@ int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* 
  * match. */
 int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth,
                              uint8_t* const* adj_out);
+
+/* fbn_autotune -- choose how each depth of fbn_learn_skeleton(_batch) on these
+ * handles counts its tables, by measurement instead of fixed rules (the
+ * paper's group-size study, Section V-D, is such a measured trade-off).  Runs
+ * the skeleton (same results as fbn_learn_skeleton_batch) once per candidate
+ * configuration -- byte histograms with 32, 64, 128 or 256 threads per test,
+ * bit planes where every small table qualifies, and, where the one-hot Gram
+ * applies, depth 0 on the Gram or on the histogram -- timing every depth with
+ * the device clock, and keeps per depth the fastest.  The choices are stored
+ * in every handle (later skeleton calls use them) and in a process-wide cache
+ * keyed by the device and the workload shape (used by handles created with
+ * FBN_TUNE_AUTO).  A choice the caller fixed in the options (group_threads,
+ * count, depth0) is not changed.  out: nullable.  The handles' results are
+ * those of the last run.  Errors as fbn_learn_skeleton_batch. */
+int fbn_autotune(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth, fbn_tuning* out);
 
 /* fbn_get_sepset -- separating set of the pair (i, j) from the last skeleton
  * (Algorithm 1, SepSet): returns |S| (0 for an empty set) and writes up to cap

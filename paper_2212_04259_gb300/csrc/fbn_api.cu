@@ -6,7 +6,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -145,6 +147,9 @@ struct Workspace {
     int* split_tab = nullptr;
     unsigned* split_ticket = nullptr;
     bool split_dirty = false;
+    // per-depth choices of the autotuner on the device, as last uploaded
+    int* d_tune = nullptr;
+    std::vector<int> tune_loaded;
     // launch geometry of the device, fixed once (kernel attributes set)
     int dev_sms = 0, grid_small = 0, grid_big = 0, grid_bits = 0;
     // the problem descriptors and vertex maps as last uploaded (skipped when
@@ -178,7 +183,7 @@ struct Workspace {
         dfree(sep_pool); dfree(gscratch); dfree(crit_keys); dfree(crit_vals); dfree(crit_dense);
         dfree(crit_dense_f);
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
-        dfree(split_tab); dfree(split_ticket);
+        dfree(split_tab); dfree(split_ticket); dfree(d_tune);
         if (events) {
             for (auto& e : kev) cudaEventDestroy(e);
             for (auto& row : tev)
@@ -260,6 +265,10 @@ struct fbn_handle {
     // row counts of the compaction on the device: [2n] counts, then [2][n + 1] row offsets
     long long* d_sep_cnt = nullptr;
     fbn_stats stats{};
+    // the autotuner's choices (empty: the fixed rules): a per-depth code
+    // (kTuneGroupMask, kTuneNoBits) and how depth 0 counts (0: the rule)
+    std::vector<int> tune;
+    int tune_depth0 = 0;
     Workspace ws;
     std::string err;
 };
@@ -308,6 +317,7 @@ int grow_workspace(fbn_handle* h, Workspace& ws, long long edge_cap, int max_n, 
         CK(dalloc(&ws.split_tab, kSplitItems * kSplitStride));
         CK(dalloc(&ws.split_ticket, kSplitItems));
         ws.split_dirty = true;
+        CK(dalloc(&ws.d_tune, kMaxDepthRecords));
     }
     if (edge_cap > ws.edge_cap) {
         dfree(ws.edges); dfree(ws.min_accept); dfree(ws.sorted);
@@ -444,11 +454,12 @@ int launch_planes(fbn_handle* h, cudaStream_t st)
 }
 
 // Whether depth 0 runs as the one-hot Gram on tensor cores.
-bool use_gram(fbn_handle* const* hs, int k)
+bool use_gram(fbn_handle* const* hs, int k, bool rule_only = false)
 {
     const fbn_handle* h = hs[0];
     if (h->opt.depth0 == FBN_DEPTH0_GRAM) return true;
     if (h->opt.depth0 == FBN_DEPTH0_HIST) return false;
+    if (!rule_only && h->tune_depth0) return h->tune_depth0 == FBN_DEPTH0_GRAM;
     long long M = 0, Nmax = 0;
     for (int p = 0; p < k; ++p) {
         M += hs[p]->M;
@@ -838,9 +849,16 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     CK(cudaMemsetAsync(ws.d_rec, 0, kMaxDepthRecords * sizeof(DepthRecord), st));
     CK(cudaMemsetAsync(ws.hist, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(ws.cursor, 0, 2 * ws.ord_cap * sizeof(unsigned long long), st));
+    if (h->tune != ws.tune_loaded) {   // the autotuner's per-depth choices
+        std::vector<int> t(kMaxDepthRecords, 0);
+        for (size_t d = 0; d < h->tune.size() && d < t.size(); ++d) t[d] = h->tune[d];
+        CK(cudaMemcpy(ws.d_tune, t.data(), t.size() * sizeof(int), cudaMemcpyHostToDevice));
+        ws.tune_loaded = h->tune;
+    }
     DepthCounters c0{};
     c0.active = 1;
     c0.bits_ok = 1;
+    c0.tune = h->tune.empty() ? nullptr : ws.d_tune;
     c0.rec = ws.d_rec;
     *ws.h_ctr = c0;
     CK(cudaMemcpyAsync(ws.d_ctr, ws.h_ctr, sizeof(DepthCounters), cudaMemcpyHostToDevice, st));
@@ -1231,6 +1249,184 @@ int run_ci(fbn_handle* h, int32_t x, int32_t y, const int32_t* z, int32_t nz, lo
     return check_status(h, *h->h_status);
 }
 
+// ---- autotuning --------------------------------------------------------
+struct TuneChoice {
+    std::vector<int> table;   // per-depth codes (empty: the fixed rules won)
+    int depth0 = 0;
+    fbn_tuning report{};
+};
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, TuneChoice> g_tune_cache;
+
+// The workload shape a tuning applies to: device, options that shape the
+// work, alpha, max depth, and every problem's (n, N, largest arity).
+std::vector<long long> tune_key(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+{
+    const fbn_handle* h = hs[0];
+    long long abits = 0;
+    std::memcpy(&abits, &alpha, sizeof abits);
+    std::vector<long long> key = {h->device, k, h->opt.form, h->opt.statistic, h->opt.df_mode, h->opt.count,
+                                  h->opt.group_threads, h->opt.depth0, h->opt.depth1, abits, max_depth};
+    for (int p = 0; p < k; ++p) {
+        key.push_back(hs[p]->n);
+        key.push_back(hs[p]->N);
+        key.push_back(hs[p]->max_arity);
+    }
+    return key;
+}
+
+void apply_tuning(fbn_handle* const* hs, int k, const std::vector<int>& table, int depth0)
+{
+    for (int p = 0; p < k; ++p) {
+        hs[p]->tune = table;
+        hs[p]->tune_depth0 = depth0;
+    }
+}
+
+// Timed skeletons of the batch under a configuration: a first run warms
+// (capture, lazily filled tables), then `reps` runs are timed with events on
+// the stream; the whole time and every depth's test window (device clock) are
+// the medians over the runs.
+int timed_run(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, const std::vector<int>& table,
+              int depth0, int reps, float* ms, fbn_stats* st)
+{
+    fbn_handle* h = hs[0];
+    apply_tuning(hs, k, table, depth0);
+    int rc = run_skeleton(hs, k, alpha, max_depth);
+    if (rc) return rc;
+    cudaEvent_t e0 = h->ws.kev[0], e1 = h->ws.kev[1];
+    std::vector<float> whole;
+    std::vector<std::vector<double>> depth(FBN_MAX_DEPTHS);
+    for (int r = 0; r < reps; ++r) {
+        CK(cudaEventRecord(e0, h->stream));
+        rc = run_skeleton(hs, k, alpha, max_depth);
+        if (rc) return rc;
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        whole.push_back(t);
+        for (int d = 0; d < FBN_MAX_DEPTHS; ++d) depth[d].push_back(h->stats.test_ms[d]);
+    }
+    auto median = [](auto v) {
+        std::sort(v.begin(), v.end());
+        return v[v.size() / 2];
+    };
+    *st = h->stats;
+    *ms = median(whole);
+    for (int d = 0; d < FBN_MAX_DEPTHS; ++d) st->test_ms[d] = median(depth[d]);
+    return FBN_OK;
+}
+
+int autotune_impl(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, fbn_tuning* out)
+{
+    fbn_handle* h = hs[0];
+    const fbn_options& o = h->opt;
+    const bool pool = o.form == FBN_FORM_POOL;
+    // candidates for the pool depths: byte histograms at each group size, and
+    // bit planes where every small table qualifies (their pool runs warp groups)
+    std::vector<int> cands;
+    if (pool && o.group_threads == 0) {
+        for (int g : {32, 64, 128, kTestThreads}) cands.push_back(g | (o.count == FBN_COUNT_BITS ? 0 : kTuneNoBits));
+        if (o.count == FBN_COUNT_AUTO) cands.push_back(0);
+    } else {
+        cands.push_back(0);
+    }
+    const bool gram_rule = pool && use_gram(hs, k, true);
+    const bool tune_d0 = pool && o.depth0 == FBN_DEPTH0_AUTO && gram_rule;
+    const int d0_rule = gram_rule ? FBN_DEPTH0_GRAM : FBN_DEPTH0_HIST;
+    fbn_tuning rep{};
+    std::vector<std::vector<double>> test_ms;
+    fbn_stats st{};
+    float ms = 0.f;
+    int depths = 0;
+    for (int c : cands) {
+        std::vector<int> table(kMaxDepthRecords, c);
+        const int rc = timed_run(hs, k, alpha, max_depth, table, d0_rule, 3, &ms, &st);
+        if (rc) return rc;
+        depths = st.depths;
+        test_ms.emplace_back(st.test_ms, st.test_ms + FBN_MAX_DEPTHS);
+        rep.candidates += 1;
+    }
+    // depth 0: the Gram against the histogram (the pool at later depths as the
+    // first candidate), by the depth's device time
+    int d0 = 0;
+    if (tune_d0) {
+        std::vector<int> table(kMaxDepthRecords, cands[0]);
+        fbn_stats sg{}, sh{};
+        int rc = timed_run(hs, k, alpha, max_depth, table, FBN_DEPTH0_GRAM, 3, &ms, &sg);
+        if (!rc) rc = timed_run(hs, k, alpha, max_depth, table, FBN_DEPTH0_HIST, 3, &ms, &sh);
+        if (rc) return rc;
+        rep.candidates += 2;
+        d0 = sh.ms[0] < sg.ms[0] ? FBN_DEPTH0_HIST : FBN_DEPTH0_GRAM;
+    }
+    // per depth the fastest candidate
+    std::vector<int> best(kMaxDepthRecords, cands[0]);
+    for (int d = 0; d < depths && d < FBN_MAX_DEPTHS; ++d) {
+        size_t bi = 0;
+        for (size_t i = 1; i < cands.size(); ++i)
+            if (test_ms[i][d] < test_ms[bi][d]) bi = i;
+        best[d] = cands[bi];
+    }
+    // the whole skeleton under the choices against the fixed rules; keep the faster
+    fbn_stats s1{};
+    float ms_fixed = 0.f, ms_tuned = 0.f;
+    int rc = timed_run(hs, k, alpha, max_depth, {}, 0, 5, &ms_fixed, &s1);
+    if (!rc) rc = timed_run(hs, k, alpha, max_depth, best, d0, 5, &ms_tuned, &s1);
+    if (rc) return rc;
+    rep.candidates += 2;
+    TuneChoice choice;
+    if (ms_tuned <= ms_fixed) {
+        choice.table = best;
+        choice.depth0 = d0;
+    }
+    const bool gram_used = choice.depth0 ? choice.depth0 == FBN_DEPTH0_GRAM : gram_rule;
+    rep.depths = depths;
+    rep.depth0 = gram_used ? FBN_DEPTH0_GRAM : FBN_DEPTH0_HIST;
+    int max_ar = 0;
+    long long max_n = 0;
+    for (int p = 0; p < k; ++p) {
+        max_ar = std::max(max_ar, hs[p]->max_arity);
+        max_n = std::max<long long>(max_n, hs[p]->N);
+    }
+    for (int d = 0; d < depths && d < FBN_MAX_DEPTHS; ++d) {
+        const int c = choice.table.empty() ? 0 : choice.table[d];
+        // bit planes only where the depth's tables can take them
+        const bool bits = !(c & kTuneNoBits) && bits_cells(h) > 0 && bits_shape_ok(d, max_ar, max_n) &&
+                          !(d == 0 && gram_used);
+        rep.count[d] = bits ? FBN_COUNT_BITS : FBN_COUNT_HIST;
+        rep.group_threads[d] = bits ? 32 : o.group_threads ? o.group_threads : (c & kTuneGroupMask);   // 0: cost model
+    }
+    rep.ms_fixed = ms_fixed;
+    rep.ms_tuned = ms_tuned;
+    choice.report = rep;
+    apply_tuning(hs, k, choice.table, choice.depth0);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[tune_key(hs, k, alpha, max_depth)] = choice;
+    }
+    if (out) *out = rep;
+    return FBN_OK;
+}
+
+// FBN_TUNE_AUTO: the first skeleton call on a shape takes the cached choices
+// of this device and shape, or tunes.
+int ensure_tuned(fbn_handle* const* hs, int k, double alpha, int32_t max_depth)
+{
+    fbn_handle* h = hs[0];
+    if (h->opt.tune != FBN_TUNE_AUTO) return FBN_OK;
+    const std::vector<long long> key = tune_key(hs, k, alpha, max_depth);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            apply_tuning(hs, k, it->second.table, it->second.depth0);
+            return FBN_OK;
+        }
+    }
+    return autotune_impl(hs, k, alpha, max_depth, nullptr);
+}
+
 void free_handle(fbn_handle* h)
 {
     if (!h) return;
@@ -1274,7 +1470,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
     o.device = -1;
     if (opt) {
         o = *opt;
-        for (int k = 0; k < 5; ++k)
+        for (int k = 0; k < 4; ++k)
             if (o.reserved[k]) return fail(nullptr, FBN_EINVAL, "reserved option field %d is nonzero", k);
         if (o.loop != FBN_LOOP_DEVICE && o.loop != FBN_LOOP_HOST) return fail(nullptr, FBN_EINVAL, "bad loop %d", o.loop);
         if (o.wait_limit < -1) return fail(nullptr, FBN_EINVAL, "bad wait_limit %d", o.wait_limit);
@@ -1290,6 +1486,7 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples, const uin
         if (o.df_mode != FBN_DF_FIXED && o.df_mode != FBN_DF_ADJUSTED)
             return fail(nullptr, FBN_EINVAL, "bad df_mode %d", o.df_mode);
         if (o.count < FBN_COUNT_AUTO || o.count > FBN_COUNT_BITS) return fail(nullptr, FBN_EINVAL, "bad count %d", o.count);
+        if (o.tune != FBN_TUNE_OFF && o.tune != FBN_TUNE_AUTO) return fail(nullptr, FBN_EINVAL, "bad tune %d", o.tune);
         if (o.depth1 == FBN_DEPTH1_TENSOR && (o.statistic != FBN_STAT_G2 || o.df_mode != FBN_DF_FIXED))
             return fail(nullptr, FBN_EINVAL, "depth1 tensor takes the G^2 statistic with fixed df only");
     }
@@ -1480,6 +1677,8 @@ int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* 
     h->learnt = false;
     fbn_handle* hs[1] = {h};
     uint8_t* outs[1] = {adj_out};
+    const int rc = ensure_tuned(hs, 1, alpha, max_depth);
+    if (rc) return rc;
     return run_skeleton(hs, 1, alpha, max_depth, outs);
 }
 
@@ -1496,7 +1695,24 @@ int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int
     }
     if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
     if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
+    const int rc = ensure_tuned(hs, k, alpha, max_depth);
+    if (rc) return rc;
     return run_skeleton(hs, k, alpha, max_depth, adj_out);
+}
+
+int fbn_autotune(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth, fbn_tuning* out)
+{
+    if (!hs || k < 1 || !hs[0]) return FBN_EINVAL;
+    fbn_handle* h = hs[0];
+    for (int p = 0; p < k; ++p) {
+        if (!hs[p]) return fail(h, FBN_EINVAL, "handle %d is NULL", p);
+        if (hs[p]->device != h->device) return fail(h, FBN_EINVAL, "handle %d is on another device", p);
+        hs[p]->learnt = false;
+        hs[p]->sep_pending = false;
+    }
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
+    if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
+    return autotune_impl(hs, k, alpha, max_depth, out);
 }
 
 int fbn_pairwise_counts(fbn_handle* h, int32_t* counts, int64_t cap)

@@ -10,7 +10,7 @@
 //
 // Each kernel runs a few milliseconds over every SM (8 CTAs of 256 threads per
 // SM), timed with CUDA events after a warm-up launch; the reductions are
-// timed for tables of 8 and 27 cells and the faster rate is the peak.  Every
+// timed for tables of 8 and 32 cells and the faster rate is the peak.  Every
 // index stays inside its buffer: the reduction kernel's columns are warp * C *
 // 32 + lane + cell * 32 with cell < C, inside C * 256 words.
 #include <cstdio>
@@ -23,10 +23,12 @@
 namespace {
 
 constexpr int kCalThreads = 256;
-constexpr int kCalMaxCells = 27;   // table sizes tried: 8 and 27 cells (a 3 x 3 x 3 table, the common depth-1 shape)
+constexpr int kCalMaxCells = 32;   // table sizes tried: 8 and 32 cells (powers of two)
 
-// cells: run-time table size <= kCalMaxCells; dynamic shared memory of
-// cells * kCalThreads words.
+// cells: run-time table size, a power of two <= kCalMaxCells; dynamic shared
+// memory of cells * kCalThreads words.  The cells come from the bytes of two
+// xorshift words (8 independent reductions per step, a few integer
+// instructions each), so the reductions, not the index arithmetic, bound it.
 __global__ void __launch_bounds__(kCalThreads) k_cal_red(const unsigned* seed, unsigned* out, int iters, int cells)
 {
     extern __shared__ int col[];
@@ -34,12 +36,15 @@ __global__ void __launch_bounds__(kCalThreads) k_cal_red(const unsigned* seed, u
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* base = col + warp * cells * 32 + lane;
-    unsigned x = seed[lane] ^ blockIdx.x;
+    const unsigned mask = (unsigned)cells - 1u;
+    unsigned x = (seed[lane] ^ blockIdx.x) | 1u, y = x * 2654435761u + 1u;
     for (int i = 0; i < iters; ++i) {
+        x ^= x << 13; x ^= x >> 17; x ^= x << 5;
+        y ^= y << 13; y ^= y >> 17; y ^= y << 5;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            x = x * 1664525u + 1013904223u;
-            atomicAdd(base + ((x >> 16) % (unsigned)cells) * 32, 1);
+        for (int k = 0; k < 4; ++k) {
+            atomicAdd(base + ((x >> (8 * k)) & mask) * 32, 1);
+            atomicAdd(base + ((y >> (8 * k)) & mask) * 32, 1);
         }
     }
     __syncthreads();

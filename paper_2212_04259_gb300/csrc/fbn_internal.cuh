@@ -80,6 +80,15 @@ struct EdgeWork {
     int64_t cnt_i, total;
 };
 
+// Per-depth codes of the autotuner (DepthCounters::tune).
+constexpr int kTuneGroupMask = 0x3FF;
+constexpr int kTuneNoBits = 0x400;
+
+__host__ __device__ __forceinline__ int tune_code(const int* tune, int d)
+{
+    return tune && d >= 0 && d < 64 ? tune[d] : 0;
+}
+
 // Edge classes: tables that fit a warp's share of shared memory run on warp
 // workers, the others on CTA workers.
 constexpr int kClassWarp = 0;
@@ -127,6 +136,9 @@ struct DepthCounters {
                                         // planes (k_edges clears it); 1 again for the next depth
     int pad_bits;
     DepthRecord* rec;                   // per-depth records (persists)
+    const int* tune;                    // per-depth choices of the autotuner, or nullptr (persists):
+                                        // kTuneGroupMask = threads per test of the small-table class (0: cost
+                                        // model), kTuneNoBits = byte histograms only at that depth
 };
 
 // Tests split by samples: when a depth has few tests against the groups, every

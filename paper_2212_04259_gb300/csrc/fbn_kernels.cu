@@ -150,7 +150,8 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
         // the small-table class runs on the bit-plane pool only if every one
         // of its edges qualifies there (all arities <= 4, d <= 1, table bound
         // within bits_cells)
-        const bool bits = bits_cells > 0 && bits_shape_ok(d, P.max_arity, P.N) && cells <= (unsigned long long)bits_cells;
+        const bool bits = bits_cells > 0 && !(tune_code(ctr->tune, d) & kTuneNoBits) && bits_shape_ok(d, P.max_arity, P.N) &&
+                          cells <= (unsigned long long)bits_cells;
         if (__any_sync(0xffffffffu, total > 0 && cls == kClassWarp && !bits) && lane == 0) ctr->bits_ok = 0;
         {   // chunk-count histogram of each class: one atomic per distinct bin in the warp
             const long long bin = total > 0 ? (long long)cls * (kMaxPasses + 1) + chunk_count(total, gs) : -1;
@@ -315,7 +316,10 @@ __global__ void k_scan(ScanClass c0, ScanClass c1, DepthCounters* ctr, double me
                     best = G;
                 }
             }
-            ctr->gsel = bits ? 32 : forced_group ? forced_group : best;   // the bit-plane pool: warp groups
+            // the bit-plane pool: warp groups; else the caller's choice, the
+            // autotuner's for this depth, or the cost model's
+            const int tuned = tune_code(ctr->tune, ctr->d) & kTuneGroupMask;
+            ctr->gsel = bits ? 32 : forced_group ? forced_group : tuned ? tuned : best;
         }
         // sample split: few single-rank tests against the groups of the class
         const int G = cls == 0 ? ctr->gsel : kTestThreads;

@@ -25,13 +25,14 @@ STATISTIC = {"g2": 0, "x2": 1}
 DF_MODE = {"fixed": 0, "adjusted": 1}
 LOOP = {"device": 0, "host": 1}
 COUNT = {"auto": 0, "hist": 1, "bits": 2}
+TUNE = {"off": 0, "auto": 1}
 MAX_DEPTHS = 64
 
 # Every symbol include/fbn.h declares.
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_orient_cpdag", "fbn_get_stats",
            "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
-           "fbn_update_data", "fbn_measure_unit_rates")
+           "fbn_update_data", "fbn_measure_unit_rates", "fbn_autotune")
 
 
 class FbnError(RuntimeError):
@@ -44,7 +45,13 @@ class Options(C.Structure):
     _fields_ = [("form", C.c_int32), ("group_size", C.c_int32), ("depth0", C.c_int32),
                 ("device", C.c_int32), ("group_threads", C.c_int32), ("wait_limit", C.c_int32),
                 ("depth1", C.c_int32), ("statistic", C.c_int32), ("df_mode", C.c_int32),
-                ("loop", C.c_int32), ("count", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("loop", C.c_int32), ("count", C.c_int32), ("tune", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("depths", C.c_int32), ("depth0", C.c_int32), ("group_threads", C.c_int32 * MAX_DEPTHS),
+                ("count", C.c_int32 * MAX_DEPTHS), ("ms_fixed", C.c_double), ("ms_tuned", C.c_double),
+                ("candidates", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -100,6 +107,8 @@ def lib():
         L.fbn_update_data.argtypes = [p, p]
         L.fbn_pairwise_counts.restype = C.c_int
         L.fbn_pairwise_counts.argtypes = [p, p, i64]
+        L.fbn_autotune.restype = C.c_int
+        L.fbn_autotune.argtypes = [p, i32, f64, i32, p]
         L.fbn_measure_unit_rates.restype = C.c_int
         L.fbn_measure_unit_rates.argtypes = [i32, p, i32]
         L.fbn_ci_test_noalloc.restype = C.c_int
@@ -155,7 +164,7 @@ def _as_u8_2d(data):
 
 def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-1,
                group_threads=0, wait_limit=0, depth1="auto", statistic="g2", df="fixed",
-               loop="device", count="auto") -> Handle:
+               loop="device", count="auto", tune="off") -> Handle:
     """Upload variable-major uint8 data [n_vars][n_samples] (numpy, or torch host/device)."""
     data, (n, N) = _as_u8_2d(data)
     ar = np.ascontiguousarray(arities, dtype=np.uint8)
@@ -163,7 +172,8 @@ def fbn_create(data, arities, form="pool", group_size=0, depth0="auto", device=-
         raise ValueError("arities must have one entry per variable")
     o = Options(form=FORMS[form], group_size=group_size, depth0=DEPTH0[depth0], device=device,
                 group_threads=group_threads, wait_limit=wait_limit, depth1=DEPTH1[depth1],
-                statistic=STATISTIC[statistic], df_mode=DF_MODE[df], loop=LOOP[loop], count=COUNT[count])
+                statistic=STATISTIC[statistic], df_mode=DF_MODE[df], loop=LOOP[loop], count=COUNT[count],
+                tune=TUNE[tune])
     out = C.c_void_p()
     rc = lib().fbn_create(_ptr(data), n, N, _ptr(ar), C.byref(o), C.byref(out))
     _check(rc)
@@ -242,6 +252,20 @@ def fbn_learn_skeleton_batch(handles, alpha: float, max_depth: int = -1, adj_out
                                         C.cast(optr, C.c_void_p))
     _check(rc, handles[0])
     return outs
+
+
+def fbn_autotune(handles, alpha: float, max_depth: int = -1) -> dict:
+    """Measure the candidate configurations on these handles and keep per depth
+    the fastest (see include/fbn.h); returns the choices."""
+    k = len(handles)
+    arr = (C.c_void_p * k)(*[hh.ptr.value if isinstance(hh.ptr, C.c_void_p) else hh.ptr for hh in handles])
+    t = Tuning()
+    _check(lib().fbn_autotune(C.cast(arr, C.c_void_p), k, float(alpha), int(max_depth), C.byref(t)), handles[0])
+    d = t.depths
+    return {"depths": d, "depth0": {1: "hist", 2: "gram"}.get(t.depth0, "auto"),
+            "group_threads": list(t.group_threads[:d]),
+            "count": [{1: "hist", 2: "bits"}.get(c, "auto") for c in t.count[:d]],
+            "ms_fixed": t.ms_fixed, "ms_tuned": t.ms_tuned, "candidates": t.candidates}
 
 
 def fbn_get_sepset(h: Handle, i: int, j: int):
