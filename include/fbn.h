@@ -209,6 +209,37 @@ int fbn_learn_skeleton(fbn_handle* h, double alpha, int32_t max_depth, uint8_t* 
 int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth,
                              uint8_t* const* adj_out);
 
+/* Callbacks of fbn_learn_skeleton_sharded, called on the calling thread.
+ * own: fill owned (uint8 [n][n], host, zeroed) with 1 at [i][j], i < j, for
+ *   every edge of adj (the graph every process shares at the start of depth
+ *   `depth`, uint8 [n][n] host, read-only) that this process tests.  Every
+ *   process's sets must partition the edges.  Return 0, nonzero to abort.
+ * exchange: gather the removal records of every process for this depth --
+ *   local: int64 [n_local][3] (i, j, rank), this process's -- into all (int64
+ *   [cap][3], host, library-owned, cap = n(n-1)/2) and set *n_all; every
+ *   process must receive the same records (in any order).  Return 0, nonzero
+ *   to abort. */
+typedef int (*fbn_shard_own_fn)(void* ctx, int32_t depth, int32_t n, const uint8_t* adj, uint8_t* owned);
+typedef int (*fbn_shard_exchange_fn)(void* ctx, int32_t depth, const int64_t* local, int64_t n_local, int64_t* all,
+                                     int64_t cap, int64_t* n_all);
+
+/* fbn_learn_skeleton_sharded -- fbn_learn_skeleton learnt by several
+ * processes together, each on its own device with its own handle on the same
+ * data, by the edge-level partition of Section IV-A across devices: at each
+ * depth every process takes the edges `own` gives it, tests them (the work
+ * pool, the same kernels), and exports its removals as (i, j, rank) records,
+ * rank the edge's lowest accepting rank in the order of Algorithm 1 with the
+ * grouping of Section IV-C; `exchange` gathers every process's records, and
+ * every process removes all of them from the same snapshot, keeping as
+ * separating set the conditioning set of the rank.  So every process ends
+ * with the adjacency and separating sets fbn_learn_skeleton gives.  One data
+ * set per handle; depth 0 runs on the work pool.  Records that name no edge
+ * of the shared graph, twice the same edge, or a rank outside the edge's
+ * rank space are refused (FBN_EINVAL).  adj_out as in fbn_learn_skeleton.
+ * Errors as fbn_learn_skeleton, FBN_EINVAL when a callback fails. */
+int fbn_learn_skeleton_sharded(fbn_handle* h, double alpha, int32_t max_depth, fbn_shard_own_fn own,
+                               fbn_shard_exchange_fn exchange, void* ctx, uint8_t* adj_out);
+
 /* fbn_autotune -- choose how each depth of fbn_learn_skeleton(_batch) on these
  * handles counts its tables, by measurement instead of fixed rules (the
  * paper's group-size study, Section V-D, is such a measured trade-off).  Runs

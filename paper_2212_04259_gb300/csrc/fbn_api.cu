@@ -150,6 +150,12 @@ struct Workspace {
     // per-depth choices of the autotuner on the device, as last uploaded
     int* d_tune = nullptr;
     std::vector<int> tune_loaded;
+    // sharded skeletons: this process's edges, removal records, their count
+    uint8_t* d_owned = nullptr;
+    long long owned_cap = 0;
+    long long* d_shard = nullptr;
+    long long shard_cap = 0;
+    unsigned long long* d_shard_count = nullptr;
     // launch geometry of the device, fixed once (kernel attributes set)
     int dev_sms = 0, grid_small = 0, grid_big = 0, grid_bits = 0;
     // the problem descriptors and vertex maps as last uploaded (skipped when
@@ -184,6 +190,7 @@ struct Workspace {
         dfree(crit_dense_f);
         dfree(gram_E); dfree(gram_G); dfree(gram_maps); dfree(gram_units); dfree(pk);
         dfree(split_tab); dfree(split_ticket); dfree(d_tune);
+        dfree(d_owned); dfree(d_shard); dfree(d_shard_count);
         if (events) {
             for (auto& e : kev) cudaEventDestroy(e);
             for (auto& row : tev)
@@ -733,6 +740,13 @@ long long find_sepset(const fbn_handle* h, int i, int j)
     return -1;
 }
 
+// Callbacks of a sharded skeleton (fbn_learn_skeleton_sharded).
+struct ShardHooks {
+    fbn_shard_own_fn own;
+    fbn_shard_exchange_fn exchange;
+    void* ctx;
+};
+
 // The depth loop of Algorithm 1 over one or more problems sharing a stream,
 // one attempt.  Every kernel of a depth takes the depth and the sizes from the
 // device counters, so the host queues depth d+1 before depth d has finished
@@ -740,7 +754,7 @@ long long find_sepset(const fbn_handle* h, int i, int j)
 // separating-set pool or global-table scratch turned out too small (both are
 // grown before returning).
 int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, bool* retry,
-                      uint8_t* const* adj_out)
+                      uint8_t* const* adj_out, const ShardHooks* shard = nullptr)
 {
     fbn_handle* h = hs[0];
     Workspace& ws = h->ws;
@@ -767,8 +781,27 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     int rc = grow_workspace(h, ws, edge_cap, max_n, k, total_vtx);
     if (rc) return rc;
     const bool plain = h->opt.form == FBN_FORM_PLAIN;
-    const bool gram = !plain && use_gram(hs, k);
-    const bool nbr1 = use_nbr1(hs, k);
+    if (shard && k != 1) return fail(h, FBN_EINVAL, "a sharded skeleton learns one problem");
+    const bool gram = !plain && !shard && use_gram(hs, k);
+    const bool nbr1 = !shard && use_nbr1(hs, k);
+    if (shard) {   // this process's edges (n x n) and the depth's removal records (3 per edge at most)
+        const long long nn = (long long)h->n * h->n;
+        if (nn > ws.owned_cap) {
+            dfree(ws.d_owned);
+            ws.d_owned = nullptr;
+            ws.owned_cap = 0;
+            CK(dalloc(&ws.d_owned, nn));
+            ws.owned_cap = nn;
+        }
+        if (edge_cap > ws.shard_cap) {
+            dfree(ws.d_shard);
+            ws.d_shard = nullptr;
+            ws.shard_cap = 0;
+            CK(dalloc(&ws.d_shard, 3 * edge_cap));
+            ws.shard_cap = edge_cap;
+        }
+        if (!ws.d_shard_count) CK(dalloc(&ws.d_shard_count, 1));
+    }
     if (nbr1) {
         rc = prepare_pack(hs, k, ws, P.data());
         if (rc) return rc;
@@ -933,7 +966,8 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     auto enqueue_head = [&]() {
         launch_snapshot(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, ws.d_ctr, st);
         launch_edges(ws.probs, ws.vtx_prob, ws.vtx_first, total_vtx, gs_forced, gs_edges, ws.binom, ws.brows, wcap,
-                     bits_cells(h), ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.hist, st);
+                     bits_cells(h), shard ? ws.d_owned : nullptr, ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr,
+                     ws.hist, st);
     };
     auto enqueue_tail = [&]() {
         launch_apply(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.binom, ws.sep_pool, ws.sep_cap, ws.d_ctr,
@@ -1005,7 +1039,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     // device-driven while loop whose body tests a depth, removes its edges,
     // ends it and lists the next depth's edges (k_gate: go on or stop).
     // Captured once per configuration: every argument it holds is in the key.
-    {
+    if (!shard) {
         std::vector<uint8_t> key;
         auto put = [&](const void* p, size_t n) {
             const uint8_t* b = (const uint8_t*)p;
@@ -1078,8 +1112,80 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
         d_loop = 2;
     }
     const bool loop = max_depth < 0 || d_loop <= max_depth;
-    const bool host_loop = h->opt.loop == FBN_LOOP_HOST;
-    if (loop && host_loop) {
+    const bool host_loop = h->opt.loop == FBN_LOOP_HOST || shard;
+    if (shard) {
+        // Several processes learn this skeleton together (Section IV-A's
+        // edge-level partition across devices): every process holds the same
+        // graph; per depth, the caller's `own` picks this process's edges, the
+        // process tests them and exports its removals as (i, j, rank) records,
+        // the caller's `exchange` gathers every process's records, and each
+        // process applies all of them to the same snapshot.  The host decides
+        // the stop, from the graph every process shares.
+        const int n = h->n;
+        std::vector<uint8_t> adj_h((size_t)n * n), own_h((size_t)n * n);
+        std::vector<int64_t> local, all;
+        for (int d = 0;; ++d) {
+            if (max_depth >= 0 && d > max_depth) break;
+            if (d >= kMaxDepthRecords - 1 || d > kMaxD) break;
+            CK(cudaMemcpyAsync(adj_h.data(), h->d_adj, adj_h.size(), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            std::vector<int> deg(n, 0);
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) deg[i] += adj_h[(size_t)i * n + j] != 0;
+            bool any = false;   // an edge with a side of at least d candidates
+            for (int i = 0; i < n && !any; ++i)
+                for (int j = i + 1; j < n && !any; ++j)
+                    any = adj_h[(size_t)i * n + j] && std::max(deg[i], deg[j]) - 1 >= d;
+            if (!any) break;
+            std::fill(own_h.begin(), own_h.end(), 0);
+            if (shard->own(shard->ctx, d, n, adj_h.data(), own_h.data()) != 0)
+                return fail(h, FBN_EINVAL, "the own callback failed at depth %d", d);
+            CK(cudaMemcpyAsync(ws.d_owned, own_h.data(), own_h.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaMemsetAsync(ws.d_shard_count, 0, sizeof(unsigned long long), st));
+            enqueue_head();
+            enqueue_tests();
+            launch_shard_export(ws.probs, ws.edges, ws.min_accept, ws.edge_cap, ws.d_ctr, ws.d_shard, ws.d_shard_count,
+                                grid_aux, st);
+            unsigned long long m = 0;
+            CK(cudaMemcpyAsync(&m, ws.d_shard_count, sizeof m, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if ((long long)m > ws.shard_cap) return fail(h, FBN_ECUDA, "removal records over their bound");
+            local.resize(3 * m);
+            if (m) CK(cudaMemcpy(local.data(), ws.d_shard, 3 * m * sizeof(int64_t), cudaMemcpyDeviceToHost));
+            const long long cap = (long long)n * (n - 1) / 2;
+            all.assign(3 * (size_t)cap, 0);
+            int64_t n_all = 0;
+            if (shard->exchange(shard->ctx, d, local.data(), (int64_t)m, all.data(), cap, &n_all) != 0 || n_all < 0 ||
+                n_all > cap)
+                return fail(h, FBN_EINVAL, "the exchange callback failed at depth %d", d);
+            // every record must name an edge of the shared graph once, with a
+            // rank inside its rank space (checked here: the kernel trusts them)
+            std::vector<uint8_t> seen((size_t)n * n, 0);
+            for (long long t = 0; t < n_all; ++t) {
+                const long long i = (long long)all[3 * t], j = (long long)all[3 * t + 1], r = (long long)all[3 * t + 2];
+                if (i < 0 || j <= i || j >= n || !adj_h[(size_t)i * n + j] || seen[(size_t)i * n + j] || r < 0)
+                    return fail(h, FBN_EINVAL, "bad removal record (%lld, %lld, %lld) at depth %d", i, j, r, d);
+                seen[(size_t)i * n + j] = 1;
+                if (d > 0) {
+                    double ti = 1, tj = 1;   // C(deg - 1, d) on each side, in double (no overflow to care about here)
+                    for (int q = 0; q < d; ++q) {
+                        ti = ti * (deg[i] - 1 - q) / (q + 1);
+                        tj = tj * (deg[j] - 1 - q) / (q + 1);
+                    }
+                    if ((double)r >= std::max(ti, 0.0) + std::max(tj, 0.0))
+                        return fail(h, FBN_EINVAL, "removal record rank %lld out of range at depth %d", r, d);
+                } else if (r != 0) {
+                    return fail(h, FBN_EINVAL, "removal record rank %lld out of range at depth 0", r);
+                }
+            }
+            if (n_all) CK(cudaMemcpyAsync(ws.d_shard, all.data(), 3 * n_all * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            launch_shard_apply(ws.probs, ws.d_shard, n_all, ws.binom, ws.brows, ws.sep_pool, ws.sep_cap, ws.d_ctr,
+                               grid_aux, st);
+            launch_depth_end(ws.d_ctr, ws.d_rec, -1, ws.hist, ws.cursor, st);
+            launch_shard_continue(ws.d_ctr, st);
+            launches += body_launches + 1;
+        }
+    } else if (loop && host_loop) {
         // the same kernels, depth by depth: the edge list, then while the
         // depth has an edge to test, its tests, removal and end, and the next
         // depth's edge list
@@ -1105,7 +1211,7 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
             if (adj_out[p])
                 CK(cudaMemcpyAsync(adj_out[p], hs[p]->d_adj, (size_t)hs[p]->n * hs[p]->n, cudaMemcpyDefault, st));
     CK(cudaStreamSynchronize(st));
-    if (loop) launches += (long long)(body_launches - (host_loop ? 1 : 0)) * std::max(0, ws.h_ctr->d - d_loop);
+    if (loop && !shard) launches += (long long)(body_launches - (host_loop ? 1 : 0)) * std::max(0, ws.h_ctr->d - d_loop);
     for (int q = 0; q < 2; ++q)
         if (direct[q]) {
             float kms = 0.f;
@@ -1180,11 +1286,12 @@ int run_skeleton_once(fbn_handle* const* hs, int k, double alpha, int32_t max_de
     return FBN_OK;
 }
 
-int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, uint8_t* const* adj_out = nullptr)
+int run_skeleton(fbn_handle* const* hs, int k, double alpha, int32_t max_depth, uint8_t* const* adj_out = nullptr,
+                 const ShardHooks* shard = nullptr)
 {
     for (int attempt = 0; attempt < 6; ++attempt) {
         bool retry = false;
-        const int rc = run_skeleton_once(hs, k, alpha, max_depth, &retry, adj_out);
+        const int rc = run_skeleton_once(hs, k, alpha, max_depth, &retry, adj_out, shard);
         if (rc || !retry) return rc;
     }
     return fail(hs[0], FBN_ENOMEM, "scratch or separating-set pool kept overflowing");
@@ -1698,6 +1805,21 @@ int fbn_learn_skeleton_batch(fbn_handle* const* hs, int32_t k, double alpha, int
     const int rc = ensure_tuned(hs, k, alpha, max_depth);
     if (rc) return rc;
     return run_skeleton(hs, k, alpha, max_depth, adj_out);
+}
+
+int fbn_learn_skeleton_sharded(fbn_handle* h, double alpha, int32_t max_depth, fbn_shard_own_fn own,
+                               fbn_shard_exchange_fn exchange, void* ctx, uint8_t* adj_out)
+{
+    if (!h) return FBN_EINVAL;
+    h->sep_pending = false;
+    h->learnt = false;
+    if (!own || !exchange) return fail(h, FBN_EINVAL, "own and exchange callbacks are required");
+    if (!(alpha > 0.0 && alpha < 1.0)) return fail(h, FBN_EINVAL, "alpha=%g outside (0, 1)", alpha);
+    if (max_depth < -1) return fail(h, FBN_EINVAL, "max_depth=%d < -1", max_depth);
+    fbn_handle* hs[1] = {h};
+    uint8_t* outs[1] = {adj_out};
+    const ShardHooks hooks{own, exchange, ctx};
+    return run_skeleton(hs, 1, alpha, max_depth, outs, &hooks);
 }
 
 int fbn_autotune(fbn_handle* const* hs, int32_t k, double alpha, int32_t max_depth, fbn_tuning* out)

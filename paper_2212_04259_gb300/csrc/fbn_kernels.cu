@@ -105,8 +105,9 @@ __device__ __forceinline__ long long binom_sat(const long long* B, int brows, in
 __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
                         const int32_t* __restrict__ vtx_first, int total_vertices, int gs_forced, long long gs_edges,
                         const long long* __restrict__ binom, int brows, long long warp_cells_cap, int bits_cells,
-                        EdgeWork* __restrict__ edges, unsigned long long* __restrict__ min_accept,
-                        long long edge_cap, DepthCounters* ctr, unsigned long long* __restrict__ hist)
+                        const uint8_t* __restrict__ owned, EdgeWork* __restrict__ edges,
+                        unsigned long long* __restrict__ min_accept, long long edge_cap, DepthCounters* ctr,
+                        unsigned long long* __restrict__ hist)
 {
     pdl_enter();
     const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -129,7 +130,9 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
         long long cnt_i = 0, total = 0;
         if (t < deg_i) {
             j = nb[t];
-            if (j > i) {
+            // owned: the edges this process tests when several share the
+            // skeleton (one problem; entry [i][j], i < j); nullptr: every edge
+            if (j > i && (owned == nullptr || owned[(long long)i * P.n + j])) {
                 if (d == 0) {
                     cnt_i = 1;
                     total = 1;
@@ -800,6 +803,102 @@ __global__ void k_apply(const ProblemDev* __restrict__ probs, const EdgeWork* __
     }
 }
 
+// Sharded skeletons (several processes test shares of one problem's edges):
+// the depth's removals of this process's edges as (i, j, lowest accepting
+// rank) records, without applying them; the oracle-equivalent test counts as
+// k_apply keeps them.
+__global__ void k_export_removed(const ProblemDev* __restrict__ probs, const EdgeWork* __restrict__ edges,
+                                 const unsigned long long* __restrict__ min_accept, long long edge_cap,
+                                 DepthCounters* ctr, long long* __restrict__ out, unsigned long long* __restrict__ count)
+{
+    pdl_enter();
+    if (!ctr->active) return;
+    const long long n0 = (long long)ctr->n_edges[0], n1 = (long long)ctr->n_edges[1];
+    unsigned long long my_tests = 0, my_samples = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n0 + n1;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long e = k < n0 ? k : edge_cap - n1 + (k - n0);
+        const EdgeWork w = edges[e];
+        const unsigned long long ma = min_accept[e];
+        const bool rm = ma < (unsigned long long)w.total;
+        const unsigned long long t = rm ? ma + 1 : (unsigned long long)w.total;
+        my_tests += t;
+        my_samples += t * (unsigned long long)probs[w.prob].N;
+        if (rm) {
+            const unsigned long long pos = atomicAdd(count, 1ULL);   // < edges of the depth <= edge_cap
+            out[3 * pos] = w.i;
+            out[3 * pos + 1] = w.j;
+            out[3 * pos + 2] = (long long)ma;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_tests += __shfl_xor_sync(0xffffffffu, my_tests, o);
+        my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_tests) atomicAdd(&ctr->tests_oracle, my_tests);
+        if (my_samples) atomicAdd(&ctr->test_samples, my_samples);
+    }
+}
+
+// Sharded skeletons: remove every process's records of the depth from the
+// snapshot (identical on every process) and keep the separating set of each:
+// the conditioning set of its rank in the order of k_edges (X-side subsets of
+// a(i)\{j} first, then Y-side subsets of a(j)\{i}, each lexicographic).
+// Records were validated on the host (i < j < n, adjacent, rank within the
+// edge's rank space).
+__global__ void k_apply_list(const ProblemDev* __restrict__ probs, const long long* __restrict__ list, long long n_list,
+                             const long long* __restrict__ binom, int brows, int32_t* __restrict__ sep_pool,
+                             long long sep_cap, DepthCounters* ctr)
+{
+    pdl_enter();
+    if (!ctr->active) return;
+    const int d = ctr->d;
+    const ProblemDev P = probs[0];
+    const long long n = P.n;
+    unsigned long long my_removed = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_list;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)list[3 * t], j = (int)list[3 * t + 1];
+        const long long ma = list[3 * t + 2];
+        my_removed += 1;
+        P.adj[i * n + j] = 0;
+        P.adj[j * n + i] = 0;
+        long long off = 0;
+        if (d > 0) {
+            const long long cnt_i = binom_sat(binom, brows, P.deg[i] - 1, d);
+            const bool xside = ma < cnt_i;
+            const int a = xside ? i : j;
+            const int posb = xside ? P.npos[(long long)i * n + j] : P.npos[(long long)j * n + i];
+            const long long lr = xside ? ma : ma - cnt_i;
+            off = (long long)atomicAdd(&ctr->sep_used, (unsigned long long)d);
+            if (off + d > sep_cap) {
+                atomicOr(&ctr->status, kStatusSepPool);
+                off = 0;
+            } else {
+                int pos[kMaxD];
+                unrank_lex(lr, P.deg[a] - 1, d, binom, pos);
+                const int32_t* nb = P.nbr + (long long)a * n;
+                for (int q = 0; q < d; ++q) sep_pool[off + q] = nb[pos[q] < posb ? pos[q] : pos[q] + 1];
+            }
+        }
+        P.sep_len[i * n + j] = d;
+        P.sep_off[i * n + j] = off;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_removed += __shfl_xor_sync(0xffffffffu, my_removed, o);
+    if ((threadIdx.x & 31) == 0 && my_removed) atomicAdd(&ctr->removed, my_removed);
+}
+
+// The next depth of a sharded skeleton runs whatever this process's share
+// held: the host decides when Algorithm 1 stops.
+__global__ void k_shard_continue(DepthCounters* ctr)
+{
+    pdl_enter();
+    if (ctr->status == 0) ctr->active = 1;
+}
+
 // End of a depth (one CTA): record it; stop when it had no edge to test (no
 // edge has a side with at least d candidates), when an error bit is set, or
 // when the next depth exceeds max_depth (>= 0); clear the per-depth counters,
@@ -950,13 +1049,13 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
 
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
                   int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
-                  long long warp_cells_cap, int bits_cells,
+                  long long warp_cells_cap, int bits_cells, const uint8_t* owned,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st)
 {
     const int warps = 8;
     launch_pdl(k_edges, dim3((total_vertices + warps - 1) / warps), dim3(warps * 32), 0, st, probs, vtx_prob,
-               vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, bits_cells, edges,
+               vtx_first, total_vertices, gs_forced, gs_edges, binom, brows, warp_cells_cap, bits_cells, owned, edges,
                min_accept, edge_cap, ctr, hist);
 }
 
@@ -992,6 +1091,24 @@ void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned
 {
     launch_pdl(k_apply, dim3(grid), dim3(256), 0, st, probs, edges, min_accept, edge_cap, binom, sep_pool, sep_cap,
                ctr);
+}
+
+void launch_shard_export(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
+                         long long edge_cap, DepthCounters* ctr, long long* out, unsigned long long* count, int grid,
+                         cudaStream_t st)
+{
+    launch_pdl(k_export_removed, dim3(grid), dim3(256), 0, st, probs, edges, min_accept, edge_cap, ctr, out, count);
+}
+
+void launch_shard_apply(const ProblemDev* probs, const long long* list, long long n_list, const long long* binom,
+                        int brows, int32_t* sep_pool, long long sep_cap, DepthCounters* ctr, int grid, cudaStream_t st)
+{
+    launch_pdl(k_apply_list, dim3(grid), dim3(256), 0, st, probs, list, n_list, binom, brows, sep_pool, sep_cap, ctr);
+}
+
+void launch_shard_continue(DepthCounters* ctr, cudaStream_t st)
+{
+    launch_pdl(k_shard_continue, dim3(1), dim3(1), 0, st, ctr);
 }
 
 void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,

@@ -19,7 +19,7 @@ void launch_snapshot(const ProblemDev* probs, const int32_t* vtx_prob, const int
                      int total_vertices, DepthCounters* ctr, cudaStream_t st);
 void launch_edges(const ProblemDev* probs, const int32_t* vtx_prob, const int32_t* vtx_first,
                   int total_vertices, int gs_forced, long long gs_edges, const long long* binom, int brows,
-                  long long warp_cells_cap, int bits_cells,
+                  long long warp_cells_cap, int bits_cells, const uint8_t* owned,
                   EdgeWork* edges, unsigned long long* min_accept, long long edge_cap, DepthCounters* ctr,
                   unsigned long long* hist, cudaStream_t st);
 // Ordering of the depth's edges, one CTA per class (nclass = 1: the small-
@@ -33,6 +33,14 @@ void launch_plain(const PoolArgs& a, int grid, size_t smem_bytes, cudaStream_t s
 void launch_apply(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
                   long long edge_cap, const long long* binom, int32_t* sep_pool, long long sep_cap,
                   DepthCounters* ctr, int grid, cudaStream_t st);
+// Sharded skeletons: this process's removals as (i, j, rank) records; the
+// union of every process's records applied to the snapshot.
+void launch_shard_export(const ProblemDev* probs, const EdgeWork* edges, const unsigned long long* min_accept,
+                         long long edge_cap, DepthCounters* ctr, long long* out, unsigned long long* count, int grid,
+                         cudaStream_t st);
+void launch_shard_apply(const ProblemDev* probs, const long long* list, long long n_list, const long long* binom,
+                        int brows, int32_t* sep_pool, long long sep_cap, DepthCounters* ctr, int grid, cudaStream_t st);
+void launch_shard_continue(DepthCounters* ctr, cudaStream_t st);
 void launch_depth_end(DepthCounters* ctr, DepthRecord* rec, int max_depth, unsigned long long* hist,
                       unsigned long long* cursor, cudaStream_t st);
 // The depth loop's condition: 1 while the next depth has an edge to test.

@@ -32,7 +32,12 @@ MAX_DEPTHS = 64
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_orient_cpdag", "fbn_get_stats",
            "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
-           "fbn_update_data", "fbn_measure_unit_rates", "fbn_autotune")
+           "fbn_update_data", "fbn_measure_unit_rates", "fbn_autotune", "fbn_learn_skeleton_sharded")
+
+# Callback types of fbn_learn_skeleton_sharded (include/fbn.h).
+OWN_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8))
+EXCHANGE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64),
+                          C.c_int64, C.POINTER(C.c_int64))
 
 
 class FbnError(RuntimeError):
@@ -107,6 +112,8 @@ def lib():
         L.fbn_update_data.argtypes = [p, p]
         L.fbn_pairwise_counts.restype = C.c_int
         L.fbn_pairwise_counts.argtypes = [p, p, i64]
+        L.fbn_learn_skeleton_sharded.restype = C.c_int
+        L.fbn_learn_skeleton_sharded.argtypes = [p, f64, i32, OWN_FN, EXCHANGE_FN, p, p]
         L.fbn_autotune.restype = C.c_int
         L.fbn_autotune.argtypes = [p, i32, f64, i32, p]
         L.fbn_measure_unit_rates.restype = C.c_int
@@ -252,6 +259,52 @@ def fbn_learn_skeleton_batch(handles, alpha: float, max_depth: int = -1, adj_out
                                         C.cast(optr, C.c_void_p))
     _check(rc, handles[0])
     return outs
+
+
+def fbn_learn_skeleton_sharded(h: Handle, alpha: float, max_depth: int, own, exchange, adj_out=None):
+    """The skeleton learnt together with other processes (include/fbn.h).
+
+    own(depth, adj) -> uint8/bool [n][n]: the edges (entries i < j) this
+    process tests at that depth, given the shared graph adj (uint8 [n][n]).
+    exchange(depth, local) -> int64 [M][3]: every process's (i, j, rank)
+    removal records of the depth, given this process's (int64 [m][3])."""
+    n = h.n
+    errors = []
+
+    def _own(_ctx, depth, n_, adj_p, owned_p):
+        try:
+            adj = np.ctypeslib.as_array(adj_p, shape=(n_, n_)).copy()
+            mask = np.ascontiguousarray(own(int(depth), adj), dtype=np.uint8)
+            if mask.shape != (n_, n_):
+                raise ValueError("own must return an [n][n] mask")
+            np.ctypeslib.as_array(owned_p, shape=(n_, n_))[:] = mask
+            return 0
+        except Exception as e:   # reported after the call
+            errors.append(e)
+            return 1
+
+    def _exchange(_ctx, depth, local_p, n_local, all_p, cap, n_all_p):
+        try:
+            local = np.ctypeslib.as_array(local_p, shape=(int(n_local), 3)).copy() if n_local else \
+                np.zeros((0, 3), dtype=np.int64)
+            every = np.ascontiguousarray(exchange(int(depth), local), dtype=np.int64).reshape(-1, 3)
+            if len(every) > cap:
+                raise ValueError("more removal records than edges")
+            if len(every):
+                np.ctypeslib.as_array(all_p, shape=(int(cap), 3))[: len(every)] = every
+            n_all_p[0] = len(every)
+            return 0
+        except Exception as e:
+            errors.append(e)
+            return 1
+
+    own_c, exch_c = OWN_FN(_own), EXCHANGE_FN(_exchange)
+    out = np.zeros((n, n), dtype=np.uint8) if adj_out is None else adj_out
+    rc = lib().fbn_learn_skeleton_sharded(h.ptr, float(alpha), int(max_depth), own_c, exch_c, None, _ptr(out))
+    if errors:
+        raise errors[0]
+    _check(rc, h)
+    return out
 
 
 def fbn_autotune(handles, alpha: float, max_depth: int = -1) -> dict:
