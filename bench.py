@@ -572,8 +572,10 @@ def main():
     for it in range(args.e2e_steps + 1):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for hh, hd in zip(hs_e2e, hosts):
-            F.fbn_update_data(hh, hd)
+        if w["kind"] == "single":
+            F.fbn_update_data(hs_e2e[0], hosts[0])
+        else:   # every problem's samples in one call (one synchronisation)
+            F.fbn_update_data_batch(hs_e2e, hosts)
         if w["kind"] == "single":
             F.fbn_learn_skeleton(hs_e2e[0], w["alpha"], w["max_depth"], adj_out=adjs_host[0])
         else:

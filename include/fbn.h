@@ -148,6 +148,15 @@ int fbn_create(const uint8_t* data, int32_t n_vars, int64_t n_samples,
  * data is then undefined until the next successful update), FBN_ECUDA. */
 int fbn_update_data(fbn_handle* h, const uint8_t* data);
 
+/* fbn_update_data_batch -- fbn_update_data on k handles of one device at
+ * once (data[p] for handle p, each in its handle's shape, host or device): the
+ * copies, the arity checks and the bit-plane builds of every data set are
+ * queued on the first handle's stream and end with one synchronisation.
+ * Errors: FBN_EINVAL, FBN_EDATA (the first offending data set is named; the
+ * data of every handle of the call is then undefined until the next
+ * successful update), FBN_ECUDA. */
+int fbn_update_data_batch(fbn_handle* const* hs, int32_t k, const uint8_t* const* data);
+
 /* fbn_set_stream -- run the handle's work on a caller-owned cudaStream_t
  * (passed as void*; NULL selects the handle's own stream).  The stream must
  * outlive its use by the handle. */

@@ -8,4 +8,4 @@ from .fbn import (FbnError, Handle, fbn_create, fbn_set_stream, fbn_ci_test, fbn
                   fbn_learn_skeleton, fbn_learn_skeleton_batch, fbn_get_sepset, fbn_export_sepsets,
                   fbn_get_stats, fbn_orient_cpdag, fbn_last_error, fbn_destroy, fbn_ci_test_noalloc,
                   fbn_pairwise_counts, fbn_update_data, fbn_measure_unit_rates, fbn_autotune,
-                  fbn_learn_skeleton_sharded, lib, LIB_PATH, EXPORTS)
+                  fbn_learn_skeleton_sharded, fbn_update_data_batch, lib, LIB_PATH, EXPORTS)

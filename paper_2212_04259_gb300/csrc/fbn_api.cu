@@ -1738,6 +1738,46 @@ int fbn_update_data(fbn_handle* h, const uint8_t* data)
     return FBN_OK;
 }
 
+int fbn_update_data_batch(fbn_handle* const* hs, int32_t k, const uint8_t* const* data)
+{
+    if (!hs || k < 1 || !hs[0] || !data) return FBN_EINVAL;
+    fbn_handle* h = hs[0];
+    for (int p = 0; p < k; ++p) {
+        if (!hs[p]) return fail(h, FBN_EINVAL, "handle %d is NULL", p);
+        if (!data[p]) return fail(h, FBN_EINVAL, "data %d is NULL", p);
+        if (hs[p]->device != h->device) return fail(h, FBN_EINVAL, "handle %d is on another device", p);
+    }
+    CK(cudaSetDevice(h->device));
+    cudaStream_t st = h->stream;
+    for (int p = 0; p < k; ++p) {   // every copy, check and bit-plane build queued on one stream
+        fbn_handle* q = hs[p];
+        q->learnt = false;
+        q->sep_pending = false;
+        CK(cudaMemcpy2DAsync(q->d_data, q->ld, data[p], q->N, q->N, q->n, cudaMemcpyDefault, st));
+        unsigned long long* bad = (unsigned long long*)q->d_ci_out;   // 8 bytes of scratch
+        CK(cudaMemsetAsync(bad, 0xff, sizeof(unsigned long long), st));
+        dim3 grid((unsigned)std::min<long long>((q->N + 255) / 256, 64), q->n);
+        k_validate<<<grid, 256, 0, st>>>(q->d_data, q->ld, q->n, q->N, q->d_ar, bad);
+        CK(cudaGetLastError());
+        const int prc = launch_planes(q, st);
+        if (prc) return fail(h, prc, "%s", q->err.c_str());
+        CK(cudaMemcpyAsync(q->h_status, bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    for (int p = 0; p < k; ++p) {
+        const fbn_handle* q = hs[p];
+        unsigned long long first_bad;
+        std::memcpy(&first_bad, q->h_status, sizeof first_bad);
+        if (first_bad != ~0ULL) {
+            const long long v = (long long)(first_bad / (unsigned long long)q->N);
+            const long long smp = (long long)(first_bad % (unsigned long long)q->N);
+            return fail(h, FBN_EDATA, "data set %d: value of variable %lld at sample %lld is >= its arity %d", p, v, smp,
+                        (int)q->h_ar[v]);
+        }
+    }
+    return FBN_OK;
+}
+
 int fbn_set_stream(fbn_handle* h, void* stream)
 {
     if (!h) return FBN_EINVAL;

@@ -32,7 +32,8 @@ MAX_DEPTHS = 64
 EXPORTS = ("fbn_create", "fbn_set_stream", "fbn_ci_test", "fbn_ci_table", "fbn_learn_skeleton",
            "fbn_learn_skeleton_batch", "fbn_get_sepset", "fbn_export_sepsets", "fbn_orient_cpdag", "fbn_get_stats",
            "fbn_last_error", "fbn_destroy", "fbn_ci_test_noalloc", "fbn_pairwise_counts",
-           "fbn_update_data", "fbn_measure_unit_rates", "fbn_autotune", "fbn_learn_skeleton_sharded")
+           "fbn_update_data", "fbn_measure_unit_rates", "fbn_autotune", "fbn_learn_skeleton_sharded",
+           "fbn_update_data_batch")
 
 # Callback types of fbn_learn_skeleton_sharded (include/fbn.h).
 OWN_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_uint8), C.POINTER(C.c_uint8))
@@ -110,6 +111,8 @@ def lib():
         L.fbn_destroy.argtypes = [p]
         L.fbn_update_data.restype = C.c_int
         L.fbn_update_data.argtypes = [p, p]
+        L.fbn_update_data_batch.restype = C.c_int
+        L.fbn_update_data_batch.argtypes = [p, i32, p]
         L.fbn_pairwise_counts.restype = C.c_int
         L.fbn_pairwise_counts.argtypes = [p, p, i64]
         L.fbn_learn_skeleton_sharded.restype = C.c_int
@@ -193,6 +196,22 @@ def fbn_update_data(h: Handle, data) -> None:
     if tuple(shape) != (h.n, h.n_samples):
         raise ValueError("data must keep the handle's shape")
     _check(lib().fbn_update_data(h.ptr, _ptr(data)), h)
+
+
+def fbn_update_data_batch(handles, datas) -> None:
+    """fbn_update_data on every handle at once (one synchronisation)."""
+    k = len(handles)
+    if len(datas) != k:
+        raise ValueError("one data set per handle")
+    keep = []
+    for hh, d in zip(handles, datas):
+        d, shape = _as_u8_2d(d)
+        if tuple(shape) != (hh.n, hh.n_samples):
+            raise ValueError("data must keep the handle's shape")
+        keep.append(d)
+    arr = (C.c_void_p * k)(*[hh.ptr.value if isinstance(hh.ptr, C.c_void_p) else hh.ptr for hh in handles])
+    dp = (C.c_void_p * k)(*[_ptr(d).value for d in keep])
+    _check(lib().fbn_update_data_batch(C.cast(arr, C.c_void_p), k, C.cast(dp, C.c_void_p)), handles[0])
 
 
 def fbn_set_stream(h: Handle, stream) -> None:
