@@ -863,6 +863,48 @@ __device__ __forceinline__ long long grp_df_adjusted(const TestSpec& s, const in
     return (long long)(grp_sum<G>(acc, red) + 0.5);
 }
 
+// One FP32 term of the bounded decisions.  G^2: n ln(N / E) with the ratio
+// N / E = (n N_++z) / (N_x+z N_+yz) from exact 64-bit integers, its log taken
+// as log1p of the exact difference over the denominator (n > 0).  X^2:
+// (n N_++z - N_x+z N_+yz)^2 / (N_++z N_x+z N_+yz) with the difference exact,
+// skipped when a margin is empty.
+__device__ __forceinline__ void g2_term(int n, int nzz, int nx, int ny, float& acc, float& mag)
+{
+    const long long a = (long long)n * nzz;
+    const long long b = (long long)nx * ny;
+    const float fb = (float)b;
+    const float delta = (float)(a - b) / fb;
+    const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
+    const float t = (float)n * L;
+    acc += t;
+    mag += fabsf(t);
+}
+
+__device__ __forceinline__ void x2_term(int n, int nzz, int nx, int ny, float& acc)
+{
+    if (nx == 0 || ny == 0) return;
+    const float fd = (float)((long long)n * nzz - (long long)nx * ny);
+    acc += fd * fd / ((float)nzz * (float)nx * (float)ny);
+}
+
+// The bounded comparison shared by the FP32 decisions: sum = the group's FP32
+// sum of the terms, mag = the sum of their magnitudes, per_thread = terms a
+// thread added, levels = the depth of the cross-thread addition tree.  The
+// error analysis is the one stated for grp_decide_bound below.  Returns 1
+// (accept), 0 (reject) or -1 (the band straddles the bracket of crit).
+__device__ __forceinline__ int decide_from_sums(float sum, float mag, float per_thread, float levels, int stat,
+                                                float crit_lo, float crit_hi)
+{
+    const float term_rel = stat == kStatX2 ? 6.0e-7f : 3.2e-7f;
+    const float rel = __fmul_ru(2.0f, __fadd_ru(term_rel, __fmul_ru(__fadd_ru(per_thread, levels), 6.0e-8f)));
+    const float scale = stat == kStatX2 ? 1.0f : 2.0f;   // G^2 = 2 sum; exact scaling
+    const float st = scale * sum;
+    const float err = __fadd_ru(__fmul_ru(__fmul_ru(__fmul_ru(scale, rel), fabsf(mag)), 1.0001f), 1e-9f);
+    if (__fadd_ru(st, err) < crit_lo) return 1;
+    if (__fadd_rd(st, -err) >= crit_hi) return 0;
+    return -1;
+}
+
 // Decision "p > alpha" as "G^2 < crit" from FP32 terms under an error bound,
 // all in FP32 (the FP64 pipe of this part is 1/64 of FP32, and every thread
 // of a group would otherwise run the bound in it).  The terms are evaluated
@@ -897,11 +939,7 @@ __device__ __forceinline__ int grp_decide_bound(const TestSpec& s, const int* T,
             const int z = c / rxy;
             const int rem = c - z * rxy;
             const int x = rem / ry, y = rem - x * ry;
-            const int nx = Nxz[z * rx + x], ny = Nyz[z * ry + y];
-            if (nx == 0 || ny == 0) continue;
-            const float fd = (float)((long long)T[c] * Nzz[z] - (long long)nx * ny);
-            const float t = fd * fd / ((float)Nzz[z] * (float)nx * (float)ny);
-            acc += t;
+            x2_term(T[c], Nzz[z], Nxz[z * rx + x], Nyz[z * ry + y], acc);
         }
         mag = acc;
     } else {
@@ -911,14 +949,7 @@ __device__ __forceinline__ int grp_decide_bound(const TestSpec& s, const int* T,
             const int z = c / rxy;
             const int rem = c - z * rxy;
             const int x = rem / ry, y = rem - x * ry;
-            const long long a = (long long)n * Nzz[z];
-            const long long b = (long long)Nxz[z * rx + x] * Nyz[z * ry + y];
-            const float fb = (float)b;
-            const float delta = (float)(a - b) / fb;
-            const float L = fabsf(delta) < 0.5f ? log1pf(delta) : logf((float)a / fb);
-            const float t = (float)n * L;
-            acc += t;
-            mag += fabsf(t);
+            g2_term(n, Nzz[z], Nxz[z * rx + x], Nyz[z * ry + y], acc, mag);
         }
     }
     float2 v = make_float2(acc, mag);
@@ -945,14 +976,7 @@ __device__ __forceinline__ int grp_decide_bound(const TestSpec& s, const int* T,
     }
     const float per_thread = (float)((C + G - 1) / G);   // exact: C < 2^24
     const float levels = (G == 32 ? 5.0f : G == 64 ? 6.0f : G == 128 ? 7.0f : 8.0f);
-    const float term_rel = stat == kStatX2 ? 6.0e-7f : 3.2e-7f;
-    const float rel = __fmul_ru(2.0f, __fadd_ru(term_rel, __fmul_ru(__fadd_ru(per_thread, levels), 6.0e-8f)));
-    const float scale = stat == kStatX2 ? 1.0f : 2.0f;   // G^2 = 2 sum; exact scaling
-    const float st = scale * v.x;
-    const float err = __fadd_ru(__fmul_ru(__fmul_ru(__fmul_ru(scale, rel), fabsf(v.y)), 1.0001f), 1e-9f);
-    if (__fadd_ru(st, err) < crit_lo) return 1;
-    if (__fadd_rd(st, -err) >= crit_hi) return 0;
-    return -1;
+    return decide_from_sums(v.x, v.y, per_thread, levels, stat, crit_lo, crit_hi);
 }
 
 }  // namespace fbn

@@ -1,5 +1,7 @@
 // fbn_kernels.cu -- per-depth kernels of the PC-stable skeleton (Algorithm 1)
-// and the single-test kernel, for sm_103a.
+// and their host launchers, for sm_103a.  The work-pool kernels live in
+// fbn_pool_small.cu, fbn_pool_bits.cu, fbn_pool_big.cu and fbn_plain.cu (device
+// code in fbn_pool.cuh); the explicit-test kernel in fbn_ci.cu.
 //
 // Depth pipeline (every kernel runs over all problems of a batch at once):
 //   k_snapshot   a(v) for every vertex: adjacency row -> ascending neighbour list
@@ -29,37 +31,20 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "fbn_device.cuh"
+#include "fbn_depth.cuh"
 #include "fbn_launch.h"
 
 namespace fbn {
-
-// Programmatic dependent launch: the kernels of a depth are launched so that
-// the next one may be scheduled once every CTA of this one has started; it
-// then waits here until this one has finished and its writes are visible.
-// Launched without the attribute, both instructions do nothing.
-__device__ __forceinline__ void pdl_enter()
-{
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 
 // Launches of the depth kernels go through launch_pdl; set_pdl(false)
 // launches them without the attribute.
 static bool g_pdl = true;
 
-// Device clock in nanoseconds, for the per-depth records.
-__device__ __forceinline__ unsigned long long gtime()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ DepthRecord* depth_rec(const DepthCounters* ctr, int d)
-{
-    return ctr->rec && d < kMaxDepthRecords ? ctr->rec + d : nullptr;
-}
+// The work-pool kernels, each defined in its own translation unit.
+__global__ void k_pool_small(PoolArgs a);
+__global__ void k_pool_bits(PoolArgs a);
+__global__ void k_pool_big(PoolArgs a);
+__global__ void k_plain(PoolArgs a);
 
 // --------------------------------------------------------------------------
 __global__ void k_snapshot(const ProblemDev* __restrict__ probs, const int32_t* __restrict__ vtx_prob,
@@ -209,13 +194,6 @@ __global__ void k_edges(const ProblemDev* __restrict__ probs, const int32_t* __r
 }
 
 // --------------------------------------------------------------------------
-// Edges of class cls: class 0 fills the edge array from the front, class 1
-// from the back.
-__device__ __forceinline__ long long class_base(const DepthCounters* ctr, int cls, long long edge_cap)
-{
-    return cls == 0 ? 0 : edge_cap - (long long)ctr->n_edges[1];
-}
-
 // One CTA: alive[k] = #edges with more than k chunks (k = 0..maxc), base[k] =
 // sum_{k' < k} alive[k'] (k = 0..maxc).  base[maxc] is the item count.
 // Block-wide scans over contiguous per-thread segments.
@@ -366,382 +344,6 @@ __global__ void k_place(const EdgeWork* __restrict__ edges, long long edge_cap, 
             first ? alive0[ch] + atomicAdd(&cursor0[ch], 1ULL) : alive1[ch] + atomicAdd(&cursor1[ch], 1ULL);
         sorted[cb + (long long)pos] = (int32_t)e;
     }
-}
-
-// --------------------------------------------------------------------------
-// Per-group state of a worker, in shared memory.
-struct GroupState {
-    long long r0, r1;
-    unsigned long long tests;
-    unsigned long long popc_work, smem_updates;   // counting work done, flushed with tests
-    unsigned long long item;   // split tests: the test's item and this group's part
-    int part;
-    unsigned ticket;
-    int e;
-    int go;
-    double crit;       // exact critical value, 0 until the exact decision needs it
-    float crit_lo, crit_hi;
-    int pos[kMaxD];
-};
-
-// Fill the test of rank rk of edge w into the group's TestSpec.  Rank 0 of
-// the group computes the subset positions (unranked when `fresh`, else the
-// successor of the previous rank of the same side); one thread per
-// conditioning variable then resolves its row.  Returns false (uniformly)
-// when the table is over the cell limit.
-template <int G, bool BITS>
-__device__ __forceinline__ bool setup_rank(const ProblemDev& P, const EdgeWork& w, int d, long long rk, bool fresh,
-                                           GroupState& S, const long long* binom, TestSpec& spec, unsigned* status)
-{
-    const int r = Grp<G>::rank();
-    const bool xside = rk < w.cnt_i;
-    const int a = xside ? w.i : w.j;
-    const int posb = xside ? w.posj : w.posi;
-    if (r == 0) {
-        if (d > 0) {
-            const long long lr = xside ? rk : rk - w.cnt_i;
-            const int p = P.deg[a] - 1;
-            if (fresh || lr == 0) unrank_lex(lr, p, d, binom, S.pos);
-            else next_subset(p, d, S.pos);
-        }
-        spec.nrows = d + 2;
-        spec.N = P.N;
-        if (BITS) spec.pstride = P.plane_ld >> 2;
-    }
-    Grp<G>::sync();
-    if (r < d + 2) {
-        int v;
-        if (r < d) {
-            const int t = S.pos[r];
-            v = P.nbr[(long long)a * P.n + (t < posb ? t : t + 1)];
-        } else {
-            v = r == d ? w.i : w.j;
-            if (r == d) spec.rx = P.ar[v]; else spec.ry = P.ar[v];
-        }
-        spec.rows[r] = P.data + (long long)v * P.ld;
-        spec.rad[r] = P.ar[v];
-        if (BITS && r < kBitsMaxD + 2) spec.prow[r] = reinterpret_cast<const uint4*>(P.planes + (long long)v * 2 * P.plane_ld);
-    }
-    Grp<G>::sync();
-    long long cells = 1;
-    for (int k = 0; k < d + 2 && cells <= kMaxCells; ++k) cells *= spec.rad[k];
-    if (cells > kMaxCells) {
-        if (r == 0) atomicOr(status, kStatusTooBig);
-        return false;
-    }
-    if (r == 0) spec.cells = cells;
-    Grp<G>::sync();
-    return true;
-}
-
-// The decision of a counted test from its table and marginals: df from the
-// declared arities or from the observed table (no degree of freedom left:
-// the test cannot reject), crit from the cache, then the bounded statistic.
-template <int G>
-__device__ __forceinline__ int decide_test(const PoolArgs& a, const TestSpec& spec, const int* T, const int* M,
-                                           GroupState& S, double* red, unsigned* status)
-{
-    const int nz = (int)spec.cells / (spec.rx * spec.ry);   // cells <= kMaxCells < 2^31: 32-bit
-    const long long df = a.df_mode ? grp_df_adjusted<G>(spec, M, red)
-                                   : (long long)((spec.rx - 1) * (spec.ry - 1)) * nz;
-    if (Grp<G>::rank() == 0) {
-        // the float bracket of crit when the table has it; else the exact
-        // value (computed and stored on first use) and its bracket
-        float2 f = make_float2(0.0f, 0.0f);
-        if (df > 0 && df < a.crit.dense_n) f = a.crit.dense_f[df];
-        S.crit = 0.0;
-        if (df > 0 && !(f.y > 0.0f)) {
-            const double c = crit_get(a.crit, df, a.alpha, status);
-            S.crit = c;
-            f = make_float2(__double2float_rd(c), __double2float_ru(c));
-        }
-        S.crit_lo = f.x;
-        S.crit_hi = f.y;
-        S.tests += 1;   // flushed to the depth counter when the group leaves the pool
-    }
-    Grp<G>::sync();
-    if (df <= 0) return 1;   // p = 1 > alpha
-    const int dec = grp_decide_bound<G>(spec, T, M, S.crit_lo, S.crit_hi, red, a.stat);
-    if (dec >= 0) return dec;
-    // the band straddles crit: exact FP64 statistic against the exact value
-    if (Grp<G>::rank() == 0 && S.crit == 0.0) S.crit = crit_get(a.crit, df, a.alpha, status);
-    Grp<G>::sync();
-    const double ex = a.stat == kStatX2 ? grp_x2_exact<G>(spec, T, M, red, nullptr) : grp_g2_exact<G>(spec, T, M, red, nullptr);
-    return ex < S.crit ? 1 : 0;
-}
-
-// Run one rank: 1 = accepts independence, 0 = rejects, -1 = could not run.
-// Counting work of one table (rank 0): C popcounts per 32-sample word from
-// bit planes, or one shared-memory update per sample by histogram.
-template <int G, bool BITS>
-__device__ __forceinline__ void note_work(GroupState& S, const TestSpec& spec)
-{
-    if (Grp<G>::rank() != 0) return;
-    if (BITS) S.popc_work += (unsigned long long)spec.cells * (unsigned long long)((spec.N + 31) >> 5);
-    else S.smem_updates += (unsigned long long)spec.N;
-}
-
-template <int G, bool BITS>
-__device__ __forceinline__ int run_rank(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w, long long rk,
-                                        bool fresh, GroupState& S, TestSpec& spec, int* slice, long long slice_ints,
-                                        int* gtab, double* red)
-{
-    unsigned* status = &a.ctr->status;
-    if (!setup_rank<G, BITS>(P, w, d, rk, fresh, S, a.binom, spec, status)) return -1;
-    int* M = nullptr;
-    const int* T = grp_table<G, BITS>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
-    if (!T) {   // the global scratch is too small: the host grows it and starts over
-        if (Grp<G>::rank() == 0) {
-            atomicOr(status, kStatusScratch);
-            atomicMax(&a.ctr->need_cells, (int)spec.cells);
-        }
-        return -1;
-    }
-    note_work<G, BITS>(S, spec);
-    grp_marginals<G>(spec, T, M);
-    return decide_test<G>(a, spec, T, M, S, red, status);
-}
-
-// One part of a split test: count samples [N p / S, N (p + 1) / S) (16-aligned
-// bounds) of rank rk into the test's global table; the part that finishes last
-// copies the table into shared memory (L2 reads), zeroes it, decides and
-// lowers the edge's rank.  Returns 1 when this group decided an acceptance.
-template <int G, bool BITS>
-__device__ __noinline__ int run_split_part(const PoolArgs& a, int d, const ProblemDev& P, const EdgeWork& w,
-                                              long long rk, int split, GroupState& S, TestSpec& spec, int* slice,
-                                              long long slice_ints, int* gtab, double* red,
-                                              const unsigned long long* min_accept_e)
-{
-    unsigned* status = &a.ctr->status;
-    const int r = Grp<G>::rank();
-    int* Tg = a.split_tab + (long long)S.item * a.split_stride;
-    if (r == 0) S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
-    Grp<G>::sync();
-    bool ready = false;   // spec holds this rank's table shape (uniform over the group)
-    if (S.go && setup_rank<G, BITS>(P, w, d, rk, true, S, a.binom, spec, status)) {
-        ready = true;
-        const long long N = P.N;
-        // part bounds on 128-sample boundaries: whole 16-byte vectors of the
-        // byte rows and whole uint4 groups of the bit planes
-        const long long lo = (N * S.part / split) & ~127LL;
-        const long long hi = S.part == split - 1 ? N : ((N * (S.part + 1) / split) & ~127LL);
-        if (r < d + 2) {
-            spec.rows[r] += lo;
-            if (BITS && r < kBitsMaxD + 2) spec.prow[r] += lo >> 7;
-        }
-        Grp<G>::sync();
-        if (r == 0) spec.N = (int)(hi - lo);
-        Grp<G>::sync();
-        int* M = nullptr;
-        const int* T = grp_table<G, BITS>(spec, slice, slice_ints, gtab, a.gscratch_ints, &M);
-        if (!T) {
-            if (r == 0) {
-                atomicOr(status, kStatusScratch);
-                atomicMax(&a.ctr->need_cells, (int)spec.cells);
-            }
-        } else {
-            note_work<G, BITS>(S, spec);
-            for (long long c = r; c < spec.cells; c += G)
-                if (T[c]) atomicAdd(Tg + c, T[c]);
-        }
-    }
-    __threadfence();
-    Grp<G>::sync();
-    if (r == 0) S.ticket = atomicAdd(&a.split_ticket[S.item], 1u);
-    Grp<G>::sync();
-    if (S.ticket != (unsigned)(split - 1)) return 0;
-    // the last part: every other part's adds are in L2; the decision needs
-    // the table's shape only (cells, radices), which this part's own setup
-    // left in spec when it counted
-    __threadfence();
-    if (!ready && !setup_rank<G, BITS>(P, w, d, rk, true, S, a.binom, spec, status)) return 0;
-    const long long C = spec.cells;
-    int* Tl = slice;
-    for (long long c = r; c < C; c += G) {
-        Tl[c] = __ldcg(Tg + c);
-        Tg[c] = 0;
-    }
-    if (r == 0) {
-        a.split_ticket[S.item] = 0;
-        S.go = (unsigned long long)rk <= *((volatile const unsigned long long*)min_accept_e);
-    }
-    Grp<G>::sync();
-    if (!S.go) return 0;
-    int* M = Tl + C;
-    grp_marginals<G>(spec, Tl, M);
-    return decide_test<G>(a, spec, Tl, M, S, red, status);
-}
-
-// Shared state of a pool CTA, sized for the most groups per CTA (8 warps).
-struct PoolShared {
-    TestSpec spec[kTestThreads / 32];
-    GroupState st[kTestThreads / 32];
-    double red[32];
-    unsigned long long base[kBaseSmem];
-};
-
-template <int G, bool BITS = false>
-__device__ __forceinline__ void pool_body(const PoolArgs& a, int* smem, PoolShared& sh)
-{
-    constexpr int NG = kTestThreads / G;   // groups per CTA
-    const DepthCounters* ctr = a.ctr;
-    const int d = ctr->d;
-    const long long maxc = (long long)ctr->maxc[a.cls];
-    const unsigned long long total = ctr->total_items[a.cls];
-    if (total == 0) return;
-    const long long cb = class_base(ctr, a.cls, a.edge_cap);
-    const EdgeWork* edges = a.edges + cb;
-    unsigned long long* min_accept = a.min_accept + cb;
-    unsigned long long* next_item = &a.ctr->next_item[a.cls];
-    const int gs = ctr->gs;
-    const int g = Grp<G>::gid();
-    const int r = Grp<G>::rank();
-    const long long slice_ints = a.smem_ints / NG;
-    int* slice = smem + g * slice_ints;
-    int* gtab = a.gscratch ? a.gscratch + ((long long)blockIdx.x * NG + g) * a.gscratch_ints : nullptr;
-    const bool base_in_smem = maxc + 1 <= kBaseSmem;
-    if (base_in_smem)
-        for (long long k = threadIdx.x; k <= maxc; k += blockDim.x) sh.base[k] = a.base[k];
-    __syncthreads();
-    const unsigned long long* base = base_in_smem ? sh.base : a.base;
-    GroupState& S = sh.st[g];
-    TestSpec& spec = sh.spec[g];
-    if (r == 0) S.tests = S.popc_work = S.smem_updates = 0;
-    const int split = ctr->split[a.cls] > 1 ? ctr->split[a.cls] : 1;
-
-    for (;;) {
-        if (r == 0) {
-            const unsigned long long wi = atomicAdd(next_item, 1ULL);
-            const unsigned long long w = split == 1 ? wi : wi / (unsigned long long)split;
-            S.item = w;
-            S.part = (int)(wi - w * (unsigned long long)split);
-            S.e = -1;
-            if (wi < total) {
-                long long lo = 0, hi = maxc - 1;   // pass k: largest k with base[k] <= w
-                while (lo < hi) {
-                    const long long mid = (lo + hi + 1) >> 1;
-                    if (base[mid] <= w) lo = mid; else hi = mid - 1;
-                }
-                const int e = a.sorted[cb + (long long)(w - base[lo])];
-                const long long tot = edges[e].total;
-                const long long cr = chunk_ranks(tot, gs);
-                const long long r0 = lo * cr;
-                S.e = e;
-                S.r0 = r0;
-                S.r1 = r0 + cr < tot ? r0 + cr : tot;
-            }
-        }
-        Grp<G>::sync();
-        const int e = S.e;
-        if (e < 0) break;
-        const EdgeWork w = edges[e];
-        const ProblemDev& P = a.probs[w.prob];
-        const long long r0 = S.r0, r1 = S.r1;
-        if (split > 1) {   // single-rank items (gs = 1, no edge above kMaxPasses ranks)
-            const int res = run_split_part<G, BITS>(a, d, P, w, r0, split, S, spec, slice, slice_ints, gtab, sh.red,
-                                                    &min_accept[e]);
-            if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)r0);
-            Grp<G>::sync();
-            continue;
-        }
-        for (long long rk = r0; rk < r1; ++rk) {
-            if (r == 0) S.go = (unsigned long long)rk <= *((volatile unsigned long long*)&min_accept[e]);
-            Grp<G>::sync();
-            if (!S.go) break;
-            const int res = run_rank<G, BITS>(a, d, P, w, rk, rk == r0, S, spec, slice, slice_ints, gtab, sh.red);
-            if (res == 1 && r == 0) atomicMin(&min_accept[e], (unsigned long long)rk);
-            if (res != 0) break;
-        }
-        Grp<G>::sync();
-    }
-    if (r == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
-    if (r == 0 && S.popc_work) atomicAdd(&a.ctr->popc_work, S.popc_work);
-    if (r == 0 && S.smem_updates) atomicAdd(&a.ctr->smem_updates, S.smem_updates);
-}
-
-// The end of a test CTA in the depth's record (the latest over CTAs).
-__device__ __forceinline__ void tests_done(const DepthCounters* ctr)
-{
-    __syncthreads();
-    if (threadIdx.x == 0)
-        if (DepthRecord* r = depth_rec(ctr, ctr->d)) atomicMax(&r->t_tests_end, gtime());
-}
-
-// Small-table class: the group size k_scan chose for this depth; byte
-// histograms (the depth's class when some edge cannot use the bit planes).
-__global__ void __launch_bounds__(kTestThreads, 3) k_pool_small(PoolArgs a)
-{
-    pdl_enter();
-    extern __shared__ int smem[];
-    __shared__ PoolShared sh;
-    if (!a.ctr->active || a.ctr->bits_ok) return;
-    switch (a.ctr->gsel) {
-        case 32: pool_body<32>(a, smem, sh); break;
-        case 64: pool_body<64>(a, smem, sh); break;
-        case 128: pool_body<128>(a, smem, sh); break;
-        default: pool_body<kTestThreads>(a, smem, sh); break;
-    }
-    tests_done(a.ctr);
-}
-
-// Small-table class counted from bit planes: the depth's class when every
-// edge qualifies (k_edges); otherwise k_pool_small runs it.  Warp groups only:
-// the fastest group size at every measured depth, and one copy of the code (the
-// kernel is sensitive to its code footprint).  CTAs per SM: 4 (64 registers a
-// thread; its 36 KB of shared memory allow it).
-#ifndef FBN_BITS_CTAS
-#define FBN_BITS_CTAS 4
-#endif
-__global__ void __launch_bounds__(kTestThreads, FBN_BITS_CTAS) k_pool_bits(PoolArgs a)
-{
-    pdl_enter();
-    extern __shared__ int smem[];
-    __shared__ PoolShared sh;
-    if (!a.ctr->active || !a.ctr->bits_ok || a.ctr->n_edges[kClassWarp] == 0) return;
-    pool_body<32, true>(a, smem, sh);   // warp groups only (k_scan sets gsel = 32): one copy of the code
-    tests_done(a.ctr);
-}
-
-// Big-table class: CTA groups.
-__global__ void __launch_bounds__(kTestThreads, 2) k_pool_big(PoolArgs a)
-{
-    pdl_enter();
-    extern __shared__ int smem[];
-    __shared__ PoolShared sh;
-    if (!a.ctr->active) return;
-    pool_body<kTestThreads>(a, smem, sh);
-    tests_done(a.ctr);
-}
-
-__global__ void __launch_bounds__(kTestThreads, 2) k_plain(PoolArgs a)
-{
-    pdl_enter();
-    extern __shared__ int smem[];
-    __shared__ TestSpec spec;
-    __shared__ GroupState S;
-    __shared__ double red[32];
-    const DepthCounters* ctr = a.ctr;
-    if (!ctr->active) return;
-    const int d = ctr->d;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && a.cls == 0)
-        if (DepthRecord* r = depth_rec(ctr, d)) r->t_tests = gtime();
-    const long long E = (long long)ctr->n_edges[a.cls];
-    const long long cb = class_base(ctr, a.cls, a.edge_cap);
-    int* gtab = a.gscratch ? a.gscratch + (long long)blockIdx.x * a.gscratch_ints : nullptr;
-    if (threadIdx.x == 0) S.tests = S.popc_work = S.smem_updates = 0;
-    for (long long e = blockIdx.x; e < E; e += gridDim.x) {
-        const EdgeWork w = a.edges[cb + e];
-        const ProblemDev& P = a.probs[w.prob];
-        for (long long rk = 0; rk < w.total; ++rk) {
-            const int res = run_rank<kTestThreads, false>(a, d, P, w, rk, rk == 0, S, spec, smem, a.smem_ints, gtab, red);
-            if (res == 1 && threadIdx.x == 0) a.min_accept[cb + e] = (unsigned long long)rk;
-            if (res != 0) break;
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0 && S.tests) atomicAdd(&a.ctr->tests, S.tests);
-    if (threadIdx.x == 0 && S.smem_updates) atomicAdd(&a.ctr->smem_updates, S.smem_updates);
-    tests_done(ctr);
 }
 
 // --------------------------------------------------------------------------
@@ -963,63 +565,6 @@ __global__ void k_gate(DepthCounters* ctr, cudaGraphConditionalHandle loop)
 }
 
 // --------------------------------------------------------------------------
-// Explicit tests (fbn_ci_test / fbn_ci_table): exact FP64 G^2 and p-value.
-template <bool BITS>
-__global__ void __launch_bounds__(kTestThreads) k_ci_tests(const ProblemDev* __restrict__ prob,
-                                                           const CiTestDesc* __restrict__ tests, int ntests,
-                                                           double* __restrict__ out, int32_t* table_out,
-                                                           int* gscratch, long long gscratch_ints,
-                                                           unsigned* status, int smem_ints, int stat, int df_mode)
-{
-    extern __shared__ int smem[];
-    __shared__ TestSpec spec;
-    __shared__ double red[32];
-    __shared__ int s_ok;
-    const int t = blockIdx.x;
-    if (t >= ntests) return;
-    const ProblemDev P = *prob;
-    if (threadIdx.x == 0) {
-        const CiTestDesc& q = tests[t];
-        const int d = q.d;
-        long long cells = 1;
-        for (int k = 0; k < d + 2; ++k) {
-            const int v = k < d ? q.z[k] : k == d ? q.x : q.y;
-            spec.rows[k] = P.data + (long long)v * P.ld;
-            spec.rad[k] = P.ar[v];
-            if (BITS && k < kBitsMaxD + 2) spec.prow[k] = reinterpret_cast<const uint4*>(P.planes + (long long)v * 2 * P.plane_ld);
-        }
-        spec.pstride = P.plane_ld >> 2;
-        spec.nrows = d + 2;
-        spec.rx = P.ar[q.x];
-        spec.ry = P.ar[q.y];
-        spec.N = P.N;
-        for (int k = 0; k < d + 2 && cells <= kMaxCells; ++k) cells *= spec.rad[k];
-        spec.cells = cells;
-        s_ok = cells <= kMaxCells;
-        if (!s_ok) atomicOr(status, kStatusTooBig);
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    int* gtab = gscratch ? gscratch + (long long)t * gscratch_ints : nullptr;
-    int* M = nullptr;
-    const int* T = grp_table<kTestThreads, BITS>(spec, smem, smem_ints, gtab, gscratch_ints, &M);
-    if (!T) {
-        if (threadIdx.x == 0) atomicOr(status, kStatusTooBig);
-        return;
-    }
-    grp_marginals<kTestThreads>(spec, T, M);
-    const double st = stat == kStatX2 ? grp_x2_exact<kTestThreads>(spec, T, M, red, table_out)
-                                      : grp_g2_exact<kTestThreads>(spec, T, M, red, table_out);
-    const double df = df_mode ? (double)grp_df_adjusted<kTestThreads>(spec, M, red)
-                              : (double)(spec.rx - 1) * (double)(spec.ry - 1) * (double)(spec.cells / (spec.rx * spec.ry));
-    if (threadIdx.x == 0) {
-        out[3 * t + 0] = st;
-        out[3 * t + 1] = df;
-        out[3 * t + 2] = df > 0.0 ? chisq_q(df, st, status) : 1.0;
-    }
-}
-
-// --------------------------------------------------------------------------
 // host launchers
 
 // Launch with programmatic stream serialisation (see pdl_enter).
@@ -1127,15 +672,6 @@ void set_pdl(bool on)
     g_pdl = on;
 }
 
-void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests, double* out,
-                     int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
-                     size_t smem_bytes, int stat, int df_mode, bool bits, cudaStream_t st)
-{
-    auto kern = bits ? k_ci_tests<true> : k_ci_tests<false>;
-    kern<<<ntests, kTestThreads, smem_bytes, st>>>(prob, tests, ntests, out, table_out, gscratch, gscratch_ints,
-                                                   status, (int)(smem_bytes / 4), stat, df_mode);
-}
-
 cudaError_t set_kernel_smem(size_t max_smem)
 {
     cudaError_t e;
@@ -1144,8 +680,7 @@ cudaError_t set_kernel_smem(size_t max_smem)
     if ((e = cudaFuncSetAttribute(k_pool_big, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k_pool_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
     if ((e = cudaFuncSetAttribute(k_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    if ((e = cudaFuncSetAttribute(k_ci_tests<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b))) return e;
-    return cudaFuncSetAttribute(k_ci_tests<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return set_ci_smem(b);
 }
 
 int pool_blocks_per_sm(int cls, size_t smem_bytes)

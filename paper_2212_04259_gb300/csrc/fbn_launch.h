@@ -1,4 +1,4 @@
-// fbn_launch.h -- host-side launchers of the kernels in fbn_kernels.cu.
+// fbn_launch.h -- host-side launchers of the depth, pool and explicit-test kernels.
 #pragma once
 
 #include <cstddef>
@@ -51,6 +51,8 @@ void launch_ci_tests(const ProblemDev* prob, const CiTestDesc* tests, int ntests
                      int32_t* table_out, int* gscratch, long long gscratch_ints, unsigned* status,
                      size_t smem_bytes, int stat, int df_mode, bool bits, cudaStream_t st);
 cudaError_t set_kernel_smem(size_t max_smem);
+// The dynamic shared-memory limit of the explicit-test kernels (fbn_ci.cu).
+cudaError_t set_ci_smem(int max_smem);
 // Sets the message fbn_last_error(NULL) returns.
 void fbn_internal_set_error(const char* msg);
 int pool_blocks_per_sm(int cls, size_t smem_bytes);
