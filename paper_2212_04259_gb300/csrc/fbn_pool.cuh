@@ -184,8 +184,11 @@ __device__ __forceinline__ int run_rank_bits(const PoolArgs& a, int d, const Pro
     const int rz = d ? spec.rad[0] : 1;
     const int df = (rx - 1) * (ry - 1) * rz;   // declared arities: >= 1
     const bool fast = a.df_mode == 0 && df < a.crit.dense_n;
+    // the bracket is read by lane 0 and broadcast: another warp may be
+    // storing it right now, and every lane must take the same branch below
+    // (the branches end in full-warp shuffles)
     float2 f = make_float2(0.0f, 0.0f);
-    if (fast) f = a.crit.dense_f[df];   // one broadcast load, in flight during the fold
+    if (fast && lane == 0) f = a.crit.dense_f[df];   // in flight during the fold
     const int z = lane >> 3, x = (lane >> 1) & 3, y = (lane & 1) * 2;
     unsigned lo = 0u, hi = 0u;
     if (z < rz) {
@@ -217,6 +220,8 @@ __device__ __forceinline__ int run_rank_bits(const PoolArgs& a, int d, const Pro
     nyhi += __shfl_xor_sync(0xffffffffu, nyhi, 4);
     nzz += __shfl_xor_sync(0xffffffffu, nzz, 4);
     if (lane == 0) S.popc_work += (unsigned long long)spec.cells * (unsigned long long)((N + 31) >> 5);
+    f.x = __shfl_sync(0xffffffffu, f.x, 0);
+    f.y = __shfl_sync(0xffffffffu, f.y, 0);
     if (fast && f.y > 0.0f) {
         float acc = 0.0f, mag = 0.0f;
         if (a.stat == kStatX2) {
@@ -232,7 +237,7 @@ __device__ __forceinline__ int run_rank_bits(const PoolArgs& a, int d, const Pro
             acc += __shfl_xor_sync(0xffffffffu, acc, o);
             mag += __shfl_xor_sync(0xffffffffu, mag, o);
         }
-        const int dec = decide_from_sums(acc, mag, 2.0f, 5.0f, a.stat, f.x, f.y);
+        const int dec = __shfl_sync(0xffffffffu, decide_from_sums(acc, mag, 2.0f, 5.0f, a.stat, f.x, f.y), 0);
         if (dec >= 0) {
             if (lane == 0) S.tests += 1;   // flushed to the depth counter when the group leaves the pool
             return dec;
