@@ -142,6 +142,25 @@ def _ptr(x):
     return C.c_void_p(x.data_ptr())
 
 
+def _need_out(t, name, np_dtype, numel):
+    """Check a caller-owned output buffer before its address goes to a C entry
+    point that writes numel elements there without knowing the buffer's size:
+    a numpy array or torch tensor (host or device) of np_dtype, contiguous,
+    writable, with at least numel elements.  Raises ValueError otherwise."""
+    if isinstance(t, np.ndarray):
+        ok = t.dtype == np_dtype and t.flags.c_contiguous and t.flags.writeable and t.size >= numel
+    else:
+        try:
+            import torch
+        except ImportError:
+            torch = None
+        ok = (torch is not None and isinstance(t, torch.Tensor) and t.is_contiguous() and t.numel() >= numel
+              and t.dtype == {np.uint8: torch.uint8, np.int32: torch.int32}[np_dtype])
+    if not ok:
+        raise ValueError(f"{name} must be a contiguous, writable {np.dtype(np_dtype).name} array or tensor "
+                         f"of at least {numel} elements")
+
+
 class Handle:
     """An fbn_handle*; destroyed on garbage collection or by fbn_destroy."""
 
@@ -257,6 +276,7 @@ def fbn_pairwise_counts(h: Handle, out=None) -> np.ndarray:
     M = int(sum(int(a) for a in h.arities))
     if out is None:
         out = np.zeros((M, M), dtype=np.int32)
+    _need_out(out, "out", np.int32, M * M)
     _check(lib().fbn_pairwise_counts(h.ptr, _ptr(out), M * M), h)
     return out
 
@@ -265,6 +285,7 @@ def fbn_learn_skeleton(h: Handle, alpha: float, max_depth: int = -1, adj_out=Non
     """Skeleton adjacency. adj_out: None (a numpy array is returned), or a
     preallocated uint8 [n][n] numpy array / torch tensor (host or device)."""
     out = np.zeros((h.n, h.n), dtype=np.uint8) if adj_out is None else adj_out
+    _need_out(out, "adj_out", np.uint8, h.n * h.n)
     _check(lib().fbn_learn_skeleton(h.ptr, float(alpha), int(max_depth), _ptr(out)), h)
     return out
 
@@ -273,6 +294,10 @@ def fbn_learn_skeleton_batch(handles, alpha: float, max_depth: int = -1, adj_out
     k = len(handles)
     arr = (C.c_void_p * k)(*[hh.ptr.value if isinstance(hh.ptr, C.c_void_p) else hh.ptr for hh in handles])
     outs = [np.zeros((hh.n, hh.n), dtype=np.uint8) for hh in handles] if adj_out is None else adj_out
+    if len(outs) != k:
+        raise ValueError("adj_out must hold one buffer per handle")
+    for p, (hh, o) in enumerate(zip(handles, outs)):
+        _need_out(o, f"adj_out[{p}]", np.uint8, hh.n * hh.n)
     optr = (C.c_void_p * k)(*[_ptr(o).value for o in outs])
     rc = lib().fbn_learn_skeleton_batch(C.cast(arr, C.c_void_p), k, float(alpha), int(max_depth),
                                         C.cast(optr, C.c_void_p))
@@ -319,6 +344,7 @@ def fbn_learn_skeleton_sharded(h: Handle, alpha: float, max_depth: int, own, exc
 
     own_c, exch_c = OWN_FN(_own), EXCHANGE_FN(_exchange)
     out = np.zeros((n, n), dtype=np.uint8) if adj_out is None else adj_out
+    _need_out(out, "adj_out", np.uint8, n * n)
     rc = lib().fbn_learn_skeleton_sharded(h.ptr, float(alpha), int(max_depth), own_c, exch_c, None, _ptr(out))
     if errors:
         raise errors[0]
